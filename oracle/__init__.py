@@ -1,0 +1,170 @@
+"""FP64 CPU oracle for the qEW explicit-Euler relaxation (arXiv:1211.7275, Sec. II-III).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package.  The product library never loads it, and it
+shares no code with the CUDA path: the arithmetic lives in ``qew_oracle.c`` (plain C, FP64,
+no fused multiply-add), this module only marshals numpy arrays through ctypes.
+
+Functions and the passages they follow:
+  philox4x32_10      Philox4x32-10 block function (Salmon et al., SC'11); the paper does not
+                     name its generator (Sec. III.B), this is the reading used throughout.
+  disorder_values    R(s,i,n) ~ N(0,1) (RF) or V(s,i,n) ~ U(-1,1) (RB) drawn at integer (i,n),
+                     Sec. III.B and the disorder cases of Sec. IV.C.
+  pinning_force      F_p(i,u): linear interpolation of R (RF) or -dV/du of the Catmull-Rom
+                     spline through V (RB), Sec. III.B.
+  rb_potential       the RB spline potential itself (spline pins only).
+  run                Euler integration of Eq. 1 (eta = c = 1, periodic in x, Sec. III.B) from
+                     the flat start (Sec. II) or a given state, with v, ubar, w2 of Eqs. 3-5.
+  lightcone          the same dynamics evaluated on a window of 2n+w sites, exact for the
+                     w central sites after n steps (stencil radius 1).
+
+Parity of every function is pinned by ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+KIND_RF = 0
+KIND_RB = 1
+KIND_NONE = 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qew_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``qew_oracle.c`` into ``oracle/liboracle.so`` (gcc, FP64, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-o", tmp, _SRC, "-lm", "-lpthread"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            lib.oracle_philox4x32_10.argtypes = [P, P, ctypes.c_int64, P]
+            lib.oracle_philox4x32_10.restype = None
+            lib.oracle_disorder_values.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, P, P,
+                                                   ctypes.c_int64, P]
+            lib.oracle_disorder_values.restype = None
+            lib.oracle_pinning_force.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, P, P,
+                                                 ctypes.c_int64, P]
+            lib.oracle_pinning_force.restype = None
+            lib.oracle_rb_potential.argtypes = [ctypes.c_uint64, ctypes.c_uint32, P, P, ctypes.c_int64, P]
+            lib.oracle_rb_potential.restype = None
+            lib.oracle_run.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.c_double, ctypes.c_uint64, P, P,
+                                       ctypes.c_int32, P, P, P, P, ctypes.c_int32]
+            lib.oracle_run.restype = ctypes.c_int
+            lib.oracle_lightcone.argtypes = [ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int64, P, P]
+            lib.oracle_lightcone.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 blocks: ``ctr`` [n,4] uint32, ``key`` [n,2] uint32 -> [n,4] uint32."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    if key.shape[0] == 1 and ctr.shape[0] > 1:
+        key = np.ascontiguousarray(np.broadcast_to(key, (ctr.shape[0], 2)))
+    out = np.empty_like(ctr)
+    _load().oracle_philox4x32_10(_p(ctr), _p(key), ctr.shape[0], _p(out))
+    return out
+
+
+def disorder_values(kind: int, seed: int, s: int, i, n) -> np.ndarray:
+    """R(s,i,n) for ``kind`` RF, V(s,i,n) for ``kind`` RB, at integer points (i, n)."""
+    i = np.ascontiguousarray(i, dtype=np.int64).ravel()
+    n = np.ascontiguousarray(n, dtype=np.int64).ravel()
+    out = np.empty(i.shape[0], np.float64)
+    _load().oracle_disorder_values(kind, seed, s, _p(i), _p(n), i.shape[0], _p(out))
+    return out
+
+
+def pinning_force(kind: int, seed: int, s: int, i, u) -> np.ndarray:
+    """F_p(i, u) of chain ``s`` for each (i, u) pair."""
+    i = np.ascontiguousarray(i, dtype=np.int64).ravel()
+    u = np.ascontiguousarray(u, dtype=np.float64).ravel()
+    out = np.empty(i.shape[0], np.float64)
+    _load().oracle_pinning_force(kind, seed, s, _p(i), _p(u), i.shape[0], _p(out))
+    return out
+
+
+def rb_potential(seed: int, s: int, i, u) -> np.ndarray:
+    """Catmull-Rom RB potential V(i, u) of chain ``s``."""
+    i = np.ascontiguousarray(i, dtype=np.int64).ravel()
+    u = np.ascontiguousarray(u, dtype=np.float64).ravel()
+    out = np.empty(i.shape[0], np.float64)
+    _load().oracle_rb_potential(seed, s, _p(i), _p(u), i.shape[0], _p(out))
+    return out
+
+
+def run(L, f, dt: float, kind, seed: int, steps, *, s=None, u0=None, n_threads: int = 0,
+        want_state: bool = False) -> dict:
+    """Relax independent periodic chains and observe them at ``steps``.
+
+    ``L``, ``f``, ``kind`` and ``s`` are per-chain sequences (scalars broadcast); ``s``
+    defaults to 0..n_chains-1.  ``u0`` is the concatenated initial state (default: flat).
+    Returns ``v``, ``ubar``, ``w2`` as [n_times, n_chains] and, with ``want_state``, the
+    concatenated final state ``u``.
+    """
+    L = np.atleast_1d(np.asarray(L, dtype=np.int64))
+    n_chains = L.shape[0]
+    f = np.ascontiguousarray(np.broadcast_to(np.asarray(f, np.float64), (n_chains,)))
+    kind = np.ascontiguousarray(np.broadcast_to(np.asarray(kind, np.int32), (n_chains,)))
+    s = np.arange(n_chains, dtype=np.uint32) if s is None else np.ascontiguousarray(
+        np.broadcast_to(np.asarray(s, np.uint32), (n_chains,)))
+    L = np.ascontiguousarray(L)
+    steps = np.ascontiguousarray(np.asarray(steps, dtype=np.int64).ravel())
+    nt = steps.shape[0]
+    v = np.empty((nt, n_chains))
+    ub = np.empty((nt, n_chains))
+    w2 = np.empty((nt, n_chains))
+    total = int(L.sum())
+    u_in = None
+    if u0 is not None:
+        u_in = np.ascontiguousarray(np.asarray(u0, np.float64).ravel())
+        if u_in.shape[0] != total:
+            raise ValueError("u0 has the wrong length")
+    u_out = np.empty(total) if want_state else None
+    rc = _load().oracle_run(n_chains, _p(L), _p(s), _p(f), _p(kind), dt, seed,
+                            _p(u_in) if u_in is not None else None, _p(steps), nt,
+                            _p(v), _p(ub), _p(w2), _p(u_out) if u_out is not None else None, n_threads)
+    if rc != 0:
+        raise ValueError(f"oracle_run failed with status {rc}")
+    out = {"v": v, "ubar": ub, "w2": w2}
+    if want_state:
+        out["u"] = u_out
+    return out
+
+
+def lightcone(L: int, s: int, f: float, dt: float, kind: int, seed: int, i0: int, w: int,
+              n_steps: int) -> tuple[np.ndarray, np.ndarray]:
+    """u and F_p at sites i0..i0+w-1 (mod L) of chain ``s`` after ``n_steps`` from the flat start."""
+    u = np.empty(w)
+    F = np.empty(w)
+    rc = _load().oracle_lightcone(L, s, f, dt, kind, seed, i0, w, n_steps, _p(u), _p(F))
+    if rc != 0:
+        raise ValueError(f"oracle_lightcone failed with status {rc}")
+    return u, F

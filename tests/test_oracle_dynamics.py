@@ -1,0 +1,175 @@
+"""Pins of the oracle's dynamics and observables against what the paper and the mathematics fix.
+
+P2  disorder-free closed form: with F_p = 0 each Fourier mode of the periodic Euler map decays
+    by lambda_k = 1 - 4 dt sin^2(pi k / L) per step and the centre of mass moves as f t
+    (Eq. 1 discretised, Sec. III.B).
+P3  the periodic Laplacian sums to zero, so ubar(step+1) - ubar(step) = dt v(step) with
+    v = f + <F_p> (Eq. 3, Sec. II).
+P4  Middleton no-passing (Sec. III.B): ordered initial states stay ordered while the Euler map
+    is monotone, 1 - 2 dt + dt dF/du >= 0 at every site.
+P7  hand-computed single steps on tiny chains, the degenerate lengths L = 1, 2, 3.
+Spline pins: the RF force interpolates R linearly between integers (Sec. III.B, Case 4 of
+    Sec. IV.C); the RB force is minus the derivative of a C^1 cubic spline through V at the
+    integers with the Catmull-Rom tangents (Cases 1-2).
+Observables: ubar, w2 against numpy's mean and population variance (Eqs. 4-5).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from qew_workloads import cosine_profile, positive_shift, random_points, random_state
+
+SEED = 12117275
+
+
+@pytest.mark.parametrize("L,k", [(64, 1), (64, 3), (63, 5), (17, 8)])
+def test_closed_form_disorder_free(orc, L, k):
+    A, B, f, dt = 0.7, 3.2, 0.37, 0.1
+    u0 = cosine_profile(L, A, B, k)
+    lam = 1.0 - 4.0 * dt * math.sin(math.pi * k / L) ** 2
+    i = np.arange(L)
+    for n in (1, 7, 50, 200):
+        out = orc.run(L, f, dt, orc.KIND_NONE, SEED, [0, n], u0=u0, want_state=True)
+        exact = B + f * n * dt + A * lam ** n * np.cos(2 * math.pi * k * i / L)
+        assert np.max(np.abs(out["u"] - exact) / np.maximum(1.0, np.abs(exact))) < 1e-12
+        assert abs(out["ubar"][1, 0] - (B + f * n * dt)) < 1e-12 * max(1.0, B + f * n * dt)
+        assert abs(out["v"][1, 0] - f) < 1e-15
+        if 2 * k != L:
+            assert abs(out["w2"][1, 0] - A * A * lam ** (2 * n) / 2) < 1e-12
+        assert abs(out["w2"][0, 0] - A * A / 2) < 1e-12
+
+
+@pytest.mark.parametrize("kind,L,f", [(0, 257, 1.0), (1, 256, 1.9), (0, 5, 0.3), (1, 3, 2.5)])
+def test_mean_velocity_invariant(orc, kind, L, f):
+    steps = list(range(0, 21)) + [100, 101, 500, 501]
+    dt = 0.1
+    out = orc.run([L, L], f, dt, kind, SEED, steps)
+    ub, v = out["ubar"], out["v"]
+    idx = [j for j in range(len(steps) - 1) if steps[j + 1] == steps[j] + 1]
+    for j in idx:
+        d = ub[j + 1] - ub[j]
+        assert np.all(np.abs(d - dt * v[j]) <= 1e-12 * np.maximum(1.0, np.abs(ub[j + 1]))), j
+    assert np.all(out["w2"][0] == 0.0)
+    assert np.all(out["ubar"][0] == 0.0)
+
+
+@pytest.mark.parametrize("kind,dt,f", [(0, 0.1, 1.0), (1, 0.02, 1.8)])
+def test_no_passing(orc, kind, dt, f):
+    L = 300
+    u0 = random_state(L, 0.5, seed=11)
+    u1 = u0 + positive_shift(L, 0.3, seed=12)
+    for n in (10, 200, 1000):
+        a = orc.run(L, f, dt, kind, SEED, [n], u0=u0, want_state=True)["u"]
+        b = orc.run(L, f, dt, kind, SEED, [n], u0=u1, want_state=True)["u"]
+        assert np.all(b >= a), n
+
+
+def test_one_step_by_hand_L3(orc):
+    # u = (0, 1, 3), f = 0.5, dt = 0.1, no disorder:
+    # lap = (1 + 3 - 0, 3 + 0 - 2, 0 + 1 - 6) = (4, 1, -5); u' = u + dt (lap + f)
+    out = orc.run(3, 0.5, 0.1, orc.KIND_NONE, SEED, [1], u0=[0.0, 1.0, 3.0], want_state=True)
+    assert np.allclose(out["u"], [0.45, 1.15, 2.55], rtol=0, atol=1e-15)
+
+
+def test_degenerate_lengths(orc):
+    # L = 1: the site is its own neighbour on both sides, lap = 0
+    out = orc.run(1, 0.5, 0.1, orc.KIND_NONE, SEED, [3], u0=[2.0], want_state=True)
+    assert abs(out["u"][0] - (2.0 + 3 * 0.05)) < 1e-15
+    # L = 2: both neighbours of a site are the other site, lap_i = 2 (u_j - u_i)
+    out = orc.run(2, 0.0, 0.1, orc.KIND_NONE, SEED, [1], u0=[0.0, 1.0], want_state=True)
+    assert np.allclose(out["u"], [0.2, 0.8], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_first_step_from_flat(orc, kind):
+    """From the flat start lap = 0 and d = 0, so u_i(1) = dt (f + F_p(i, 0))."""
+    L, f, dt = 97, 0.8, 0.1
+    out = orc.run(L, f, dt, kind, SEED, [1], s=[4], want_state=True)
+    i = np.arange(L)
+    F0 = orc.pinning_force(kind, SEED, 4, i, np.zeros(L))
+    assert np.allclose(out["u"], dt * (f + F0), rtol=0, atol=1e-15)
+    if kind == 0:
+        assert np.array_equal(F0, orc.disorder_values(0, SEED, 4, i, np.zeros(L)))
+
+
+def test_rf_force_is_linear_interpolation(orc):
+    i, n = random_points(2000, 1 << 20, -40, 40, seed=21)
+    R0 = orc.disorder_values(0, SEED, 2, i, n)
+    R1 = orc.disorder_values(0, SEED, 2, i, n + 1)
+    # nodes
+    assert np.array_equal(orc.pinning_force(0, SEED, 2, i, n.astype(float)), R0)
+    # continuity at the upper node
+    below = orc.pinning_force(0, SEED, 2, i, (n + 1).astype(float) - 1e-12)
+    assert np.allclose(below, R1, atol=1e-10, rtol=0)
+    # straight line in between: equal second differences vanish
+    d = np.array([0.1, 0.35, 0.6, 0.85])
+    F = np.stack([orc.pinning_force(0, SEED, 2, i, n + x) for x in d])
+    assert np.allclose(F[1] - F[0], F[3] - F[2], atol=1e-12)
+    assert np.allclose(F[2] - F[1], F[1] - F[0], atol=1e-12)
+    # slope equals the node difference
+    assert np.allclose((F[3] - F[0]) / 0.75, R1 - R0, atol=1e-11)
+
+
+def test_rb_spline_pins(orc):
+    i, n = random_points(2000, 1 << 18, -40, 40, seed=22)
+    s = 6
+    V = [orc.disorder_values(1, SEED, s, i, n + k) for k in (-1, 0, 1, 2)]
+    nf = n.astype(float)
+    # the potential interpolates the drawn values at the integers
+    assert np.allclose(orc.rb_potential(SEED, s, i, nf), V[1], atol=1e-15, rtol=0)
+    assert np.allclose(orc.rb_potential(SEED, s, i, nf + 1 - 1e-13), V[2], atol=1e-11, rtol=0)
+    # Catmull-Rom tangents: F(n) = -(V(n+1) - V(n-1)) / 2, F(n+1-) = -(V(n+2) - V(n)) / 2
+    assert np.allclose(orc.pinning_force(1, SEED, s, i, nf), -(V[2] - V[0]) / 2, atol=1e-15)
+    assert np.allclose(orc.pinning_force(1, SEED, s, i, nf + 1 - 1e-13), -(V[3] - V[1]) / 2, atol=1e-11)
+    # the force is quadratic in the cell: 3-point Gauss-Legendre integrates it exactly, and
+    # its integral over the cell is -(V(n+1) - V(n))
+    x, w = np.polynomial.legendre.leggauss(3)
+    integral = sum(wk * orc.pinning_force(1, SEED, s, i, nf + 0.5 + 0.5 * xk) for xk, wk in zip(x, w)) * 0.5
+    assert np.allclose(integral, -(V[2] - V[1]), atol=1e-14)
+    # F = -dV/du inside the cell (central difference of the potential)
+    h = 1e-5
+    for d in (0.2, 0.5, 0.77):
+        Fd = orc.pinning_force(1, SEED, s, i, nf + d)
+        dV = (orc.rb_potential(SEED, s, i, nf + d + h) - orc.rb_potential(SEED, s, i, nf + d - h)) / (2 * h)
+        assert np.allclose(Fd, -dV, atol=1e-8)
+
+
+def test_observables_match_numpy(orc):
+    L = 1000
+    u0 = random_state(L, 2.0, seed=31)
+    f = 0.6
+    out = orc.run(L, f, 0.1, 0, SEED, [0], u0=u0)
+    assert abs(out["ubar"][0, 0] - np.mean(u0)) < 1e-12 * max(1, abs(np.mean(u0)))
+    assert abs(out["w2"][0, 0] - np.var(u0)) < 1e-10 * np.var(u0)
+    F = orc.pinning_force(0, SEED, 0, np.arange(L), u0)
+    assert abs(out["v"][0, 0] - (f + np.mean(F))) < 1e-13
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_lightcone_equals_periodic_run(orc, kind):
+    L, n, w = 101, 20, 7
+    full = orc.run(L, 1.2, 0.1, kind, SEED, [n], s=[3], want_state=True)["u"]
+    Ffull = orc.pinning_force(kind, SEED, 3, np.arange(L), full)
+    for i0 in (0, 50, 97, L - 1):
+        u, F = orc.lightcone(L, 3, 1.2, 0.1, kind, SEED, i0, w, n)
+        idx = (i0 + np.arange(w)) % L
+        assert np.array_equal(u, full[idx])
+        assert np.array_equal(F, Ffull[idx])
+
+
+def test_chains_are_independent_and_keyed_by_sample(orc):
+    L = 64
+    both = orc.run([L, L], 1.0, 0.1, 0, SEED, [100], s=[0, 1], want_state=True)["u"]
+    one = orc.run(L, 1.0, 0.1, 0, SEED, [100], s=[1], want_state=True)["u"]
+    assert np.array_equal(both[L:], one)
+    assert not np.array_equal(both[:L], both[L:])
+
+
+def test_rejects_bad_arguments(orc):
+    with pytest.raises(ValueError):
+        orc.run(8, 1.0, 0.1, 0, SEED, [5, 3])
+    with pytest.raises(ValueError):
+        orc.run(0, 1.0, 0.1, 0, SEED, [1])
+    with pytest.raises(ValueError):
+        orc.lightcone(10, 0, 1.0, 0.1, 0, SEED, 0, 3, 4)

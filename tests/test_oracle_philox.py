@@ -1,0 +1,152 @@
+"""Pins of the oracle's random numbers.
+
+Philox4x32-10 (Salmon et al., SC'11) is pinned bit for bit against an independent
+implementation: the cuRAND host generator for PHILOX4_32_10, run on the CPU.  Its output block
+j at generator offset o is, with B = o/4 + j, the Philox block of key (lo32(seed), hi32(seed))
+and counter (lo32(B >> 16), lo32(B >> 48), B mod 2^16, 0) (established by search over
+counters), so arbitrary keys and counter words 0-2 are exercised; word 3 enters the first
+round exactly like word 1 and is exercised from the second round on.
+
+The transforms to R ~ N(0,1) (random field) and V ~ U(-1,1) (random bond) are pinned by
+their distributions (Kolmogorov-Smirnov against scipy), their independence across the
+integer lattice (i, n), and by which output word decides what (sign of R from word 1, V
+increasing in word 0).  The paper fixes only the distributions (Sec. II, Sec. IV.C).
+"""
+import ctypes
+import ctypes.util
+import os
+
+import numpy as np
+import pytest
+
+from qew_workloads import random_points
+
+scipy_stats = pytest.importorskip("scipy.stats")
+
+
+def _curand():
+    for cand in ("/usr/local/cuda/lib64/libcurand.so.10", "/usr/local/cuda/lib64/libcurand.so",
+                 ctypes.util.find_library("curand")):
+        if cand and (os.path.exists(cand) or not cand.startswith("/")):
+            try:
+                return ctypes.CDLL(cand)
+            except OSError:
+                continue
+    return None
+
+
+def _curand_words(lib, seed, offset, n):
+    gen = ctypes.c_void_p()
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # PHILOX4_32_10
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
+        buf = np.zeros(n, np.uint32)
+        assert lib.curandGenerate(gen, buf.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(n)) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    return buf.reshape(-1, 4)
+
+
+@pytest.mark.parametrize("seed,block0", [
+    (0, 0),
+    (12117275, 0),
+    (0xFFFFFFFFFFFFFFFF, 123456),
+    (0xDEADBEEF12345678, (1 << 48) - 40000),  # word 0 wraps, word 1 becomes 1
+    (0x0123456789ABCDEF, (7 << 48) + (0xFFFF0000 << 16) + 12345),
+])
+def test_philox_matches_curand_host(orc, seed, block0):
+    lib = _curand()
+    if lib is None:
+        pytest.skip("cuRAND host library not available")
+    nb = 1 << 16
+    ref = _curand_words(lib, seed, 4 * block0, 4 * nb)
+    b = np.arange(nb, dtype=np.uint64) + np.uint64(block0)
+    m32 = np.uint64(0xFFFFFFFF)
+    ctr = np.zeros((nb, 4), np.uint32)
+    ctr[:, 0] = ((b >> np.uint64(16)) & m32).astype(np.uint32)
+    ctr[:, 1] = ((b >> np.uint64(48)) & m32).astype(np.uint32)
+    ctr[:, 2] = (b & np.uint64(0xFFFF)).astype(np.uint32)
+    key = np.array([[seed & 0xFFFFFFFF, seed >> 32]], np.uint32)
+    out = orc.philox4x32_10(ctr, key)
+    assert np.array_equal(out, ref)
+
+
+def _words(orc, seed, s, i, n, tag):
+    ctr = np.stack([i.astype(np.uint32), n.astype(np.int32).view(np.uint32),
+                    np.full(i.shape, s, np.uint32), np.full(i.shape, tag, np.uint32)], axis=1)
+    return orc.philox4x32_10(ctr, np.array([[seed & 0xFFFFFFFF, seed >> 32]], np.uint32))
+
+
+def test_rf_values_standard_normal(orc):
+    i, n = random_points(200_000, 1 << 25, -50, 5000, seed=1)
+    r = orc.disorder_values(orc.KIND_RF, 12117275, 3, i, n)
+    ks = scipy_stats.kstest(r, "norm")
+    assert ks.pvalue > 1e-3, ks
+    assert abs(r.mean()) < 5 / np.sqrt(r.size)
+    assert abs(r.var() - 1.0) < 0.02
+
+
+def test_rb_values_uniform(orc):
+    i, n = random_points(200_000, 1 << 16, -100, 100, seed=2)
+    v = orc.disorder_values(orc.KIND_RB, 12117275, 7, i, n)
+    assert np.all(v > -1.0) and np.all(v < 1.0)
+    ks = scipy_stats.kstest(v, "uniform", args=(-1.0, 2.0))
+    assert ks.pvalue > 1e-3, ks
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_values_uncorrelated_on_lattice(orc, kind):
+    m = 50_000
+    i, n = random_points(m, 1 << 20, -1000, 1000, seed=3)
+    base = orc.disorder_values(kind, 99, 0, i, n)
+    for di, dn, ds in [(0, 1, 0), (1, 0, 0), (0, 0, 1), (0, -1, 0)]:
+        other = orc.disorder_values(kind, 99, ds, i + di, n + dn)
+        rho = np.corrcoef(base, other)[0, 1]
+        assert abs(rho) < 5 / np.sqrt(m), (di, dn, ds, rho)
+
+
+def test_rf_sign_follows_word1(orc):
+    """R = sqrt(-2 ln U1) cos(2 pi U2) is positive exactly when U2 lies in the outer quarters."""
+    seed, s = 424242, 5
+    i, n = random_points(100_000, 1 << 22, -300, 300, seed=4)
+    r = orc.disorder_values(orc.KIND_RF, seed, s, i, n)
+    w = _words(orc, seed, s, i, n, 0)
+    x1 = w[:, 1].astype(np.uint64)
+    inner = (x1 >= (1 << 30)) & (x1 < 3 * (1 << 30))
+    far = np.abs(x1.astype(np.int64) - (1 << 30)) > 64
+    far &= np.abs(x1.astype(np.int64) - 3 * (1 << 30)) > 64
+    assert np.all((r[far] < 0) == inner[far])
+
+
+def test_rf_magnitude_follows_word0(orc):
+    """Among points with the same cosine factor, |R| decreases as word 0 (U1) grows."""
+    seed, s = 31337, 1
+    i, n = random_points(400_000, 1 << 22, -300, 300, seed=5)
+    r = orc.disorder_values(orc.KIND_RF, seed, s, i, n)
+    w = _words(orc, seed, s, i, n, 0)
+    # cos(2 pi U2) ~ 1 when word 1 is within 2^24 of 0 or 2^32
+    sel = (w[:, 1] < (1 << 24)) | (w[:, 1] > 0xFFFFFFFF - (1 << 24))
+    x0 = w[sel, 0]
+    mag = np.abs(r[sel])
+    order = np.argsort(x0)
+    ratio = mag[order] / np.sqrt(-2.0 * np.log((x0[order].astype(np.float64) + 0.5) * 2.0 ** -32))
+    assert np.all(ratio > 0.98) and np.all(ratio <= 1.0 + 1e-12)
+
+
+def test_rb_increasing_in_word0(orc):
+    seed, s = 2024, 9
+    i, n = random_points(100_000, 1 << 22, -300, 300, seed=6)
+    v = orc.disorder_values(orc.KIND_RB, seed, s, i, n)
+    w = _words(orc, seed, s, i, n, 1)
+    order = np.argsort(w[:, 0], kind="stable")
+    assert np.all(np.diff(v[order]) >= 0)
+    assert np.all((v >= 0) == (w[:, 0] >= (1 << 31)))
+
+
+def test_rf_and_rb_streams_differ(orc):
+    """The tag word separates the random-field and random-bond streams at the same point."""
+    i, n = random_points(1000, 1 << 20, 0, 100, seed=7)
+    w0 = _words(orc, 5, 0, i, n, 0)
+    w1 = _words(orc, 5, 0, i, n, 1)
+    assert np.mean(np.all(w0 == w1, axis=1)) == 0.0
