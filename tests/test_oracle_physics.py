@@ -1,0 +1,70 @@
+"""P5: rough physics pin of the oracle against the paper's printed slopes.
+
+At the finite-size critical force f_c^L (random field, L = 4096, found with the oracle alone by
+``tests/golden/make_fc_rf_oracle.py`` from the decade 50 < t < 500), the relaxation from the
+flat start must show the paper's mesoscopic behaviour (Sec. IV.B, Fig. 5):
+  - v decays with an effective exponent of about 0.16 for 1 < t < 30 (a window the bisection
+    did not use);
+  - w grows with an effective exponent between about 0.67 and 0.84, i.e. w2 with 1.3 .. 1.7;
+and the transition must be there: below f_c the velocity collapses, above it saturates
+(Sec. III.A).  Tolerances are wide: these are effective exponents on a small system.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from qew_workloads import SEED, log_spaced_steps
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _load(name):
+    with open(os.path.join(HERE, "golden", name)) as fh:
+        return json.load(fh)
+
+
+def _slope(t, y, lo, hi):
+    sel = (t >= lo) & (t <= hi)
+    return np.polyfit(np.log(t[sel]), np.log(y[sel]), 1)[0]
+
+
+@pytest.fixture(scope="module")
+def runs(orc):
+    fc = _load("fc_rf_L4096.json")
+    steps = log_spaced_steps(fc["n_steps"], 30, include_zero=False)
+    t = steps * fc["dt"]
+    out = {}
+    for label, f in (("fc", fc["f_c"]), ("below", fc["f_c"] - 0.1), ("above", fc["f_c"] + 0.2)):
+        r = orc.run([fc["L"]] * fc["samples"], f, fc["dt"], orc.KIND_RF, fc["seed"], steps)
+        out[label] = (r["v"].mean(axis=1), r["w2"].mean(axis=1))
+    return t, out
+
+
+def test_short_time_velocity_exponent(runs):
+    paper = _load("paper_values.json")["effective_slopes"]
+    t, out = runs
+    V, _ = out["fc"]
+    s = -_slope(t, V, 1, 30)
+    assert abs(s - paper["v_short"]) < 0.04, s
+
+
+def test_width_exponent(runs):
+    paper = _load("paper_values.json")["effective_slopes"]
+    t, out = runs
+    _, W2 = out["fc"]
+    s = _slope(t, W2, 50, 500)
+    assert 2 * paper["w_short"] - 0.05 < s < 2 * paper["w_long"] + 0.05, s
+
+
+def test_transition_brackets(runs):
+    t, out = runs
+    assert -_slope(t, out["below"][0], 50, 500) > 0.3
+    assert abs(_slope(t, out["above"][0], 50, 500)) < 0.05
+
+
+def test_fc_fixture_provenance():
+    fc = _load("fc_rf_L4096.json")
+    assert fc["_made_by"].startswith("tests/golden/make_fc_rf_oracle.py")
+    assert fc["seed"] == SEED
