@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Throughput of the qEW explicit-Euler relaxation (arXiv:1211.7275, Sec. II-III) on GB300.
+
+Metric: site-updates/s = sum over chains of L x Euler steps, divided by the device time of the
+relaxation.  One bench step is one full pass of the hot path over the workload: reset to the flat
+start, integrate `relax_steps` Euler steps with the fused FP32-split kernel, record v and w2 at
+log-spaced observation steps (fused reductions) and bring them to the host.
+
+Default workload: 4 random-field chains of L = 2^25 (the paper's largest size, Sec. IV.D), dt = 0.1,
+drive at the preset's critical force.  The 4 GiB state is larger than the 129 MB L2, so no flush
+is needed between steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle instead (the baseline arm).
+Under torchrun (N > 1) each rank relaxes its own independent samples (weak scaling, no collective
+on the data path); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import qew_workloads as W  # noqa: E402
+
+METRIC = "site-updates/s and % binding roofline, qEW Euler at L=2^25, FP32-split vs FP64, 1 GB300"
+UNIT = "site-updates/s"
+
+# Algorithmic lane operations per site-update of the fused kernel (derivation in the design doc):
+# elastic force 5, pinning 2 (RF) / 2 (RB) / 0 (none), Euler 2, cell test 1; plus, per cell
+# crossing, one Philox4x32-10 block (10 rounds x 6) and the value transform.
+OPS_BASE = {0: 10, 1: 10, 2: 8}
+OPS_PER_CROSSING = {0: 90, 1: 62, 2: 0}
+LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="rf_4x2^25", choices=["rf_4x2^25", "rf_16x2^20", "rb_1024x2^16",
+                                                                "tiny_rf_1x1024"])
+    p.add_argument("--relax-steps", type=int, default=4096)
+    p.add_argument("--n-obs", type=int, default=12)
+    p.add_argument("--tuning", default="auto", help="'auto' or tile_w,K,tiles_per_cta")
+    p.add_argument("--fp64-steps", type=int, default=256, help="Euler steps of the FP64 comparison leg (0: skip)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload(name: str, rank: int):
+    p = W.PRESETS[name]
+    return dict(name=name, L=p["L"], batch=p["batch"], kind=p["kind"], f=W.preset_f(name), dt=p["dt"],
+                seed=W.SEED + 1000003 * rank)
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def bus_id(dev: int) -> str | None:
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        return f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("qew_split.cu", "qew_device.cuh", "qew_internal.h"):
+        with open(os.path.join(ROOT, "paper_1211_7275_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload_name: str):
+    """DRAM bytes per site-update of the fused kernel from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "fused_split_kernel.traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_sha") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_site_update", {}).get(workload_name)
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (baseline leg / reference arm)
+# ------------------------------------------------------------------------------------------
+def oracle_sample(wl: dict, w: int, n_steps: int) -> dict:
+    """Time the CPU oracle on windows of the same chains: one light-cone window of w sites per host
+    thread, n_steps Euler steps each (exact sites of the full-size chains)."""
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    L = wl["L"]
+    jobs = [(t % wl["batch"], (t * w * 7919) % L) for t in range(cores)]
+    errs = []
+
+    def work(c, i0):
+        try:
+            oracle.lightcone(L, c, wl["f"], wl["dt"], wl["kind"], wl["seed"], i0, w, n_steps)
+        except Exception as e:  # pragma: no cover
+            errs.append(e)
+
+    ths = [threading.Thread(target=work, args=j) for j in jobs]
+    t0 = time.perf_counter()
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    dt = time.perf_counter() - t0
+    if errs:
+        raise errs[0]
+    updates = cores * w * n_steps
+    return {"value": updates / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} threads x one light-cone window of {w} sites x {n_steps} Euler steps of the "
+                      f"{wl['name']} chains (exact sites of the full-size chains), {dt:.1f} s",
+            "seconds": dt}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    wl = workload(args.workload, 0)
+    w, n = 1 << 17, 4
+    for _ in range(args.warmup):
+        oracle_sample(wl, w, n)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = oracle_sample(wl, w, n)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    cores = r["cores"]
+    total = sum(cores * w * n for _ in vals)
+    value = total / sum(secs)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "L": wl["L"], "batch": wl["batch"], "kind": wl["kind"], "f": wl["f"],
+                   "dt": wl["dt"], "arm": "CPU FP64 oracle (plain C, one light-cone window per host thread)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": r["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def main() -> None:
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_1211_7275_gb300 as q
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    wl = workload(args.workload, rank)
+    sched = W.log_spaced_steps(args.relax_steps, args.n_obs)
+    stream = torch.cuda.current_stream()
+    relax = q.Relaxation(wl["L"], wl["f"], wl["kind"], dt=wl["dt"], seed=wl["seed"], precision=q.FP32_SPLIT,
+                         batch=wl["batch"], stream=stream)
+    if args.tuning == "auto":
+        relax.set_tuning(0, 0, 0)
+    else:
+        relax.set_tuning(*[int(x) for x in args.tuning.split(",")])
+
+    def one_step():
+        relax.reset()
+        relax.observe(sched)
+
+    for _ in range(max(args.warmup, 3)):
+        one_step()
+    tuning = relax.tuning()
+
+    sampler = ClockSampler(bus_id(local))
+    relax.enable_stats(True)
+    torch.cuda.synchronize()
+    barrier()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    st = relax.stats()
+    relax.enable_stats(False)
+    n_sites = relax.n_sites
+    updates = n_sites * args.relax_steps * args.steps
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    total_updates = updates * world
+    value = total_updates / (ms_max / 1e3)
+
+    # ---- roofline of the fused kernel, from its own event-timed launches ----
+    peaks = load_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    clk = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    per_launch_ms = st["fused_ms"] / max(1, st["fused_launches"])
+    su_per_launch = st["site_updates"] / max(1, st["fused_launches"])
+    r_cross = st["crossings"] / max(1, st["site_updates"])
+    kind = wl["kind"]
+    ops_per_su = OPS_BASE[kind] + OPS_PER_CROSSING[kind] * r_cross
+    achieved = ops_per_su * su_per_launch / (per_launch_ms / 1e3) / 1e12
+    peak = sms * LANES_PER_SM * clk * 1e6 / 1e12
+    tile_w, K, tpc = tuning
+    bytes_per_su = 2 * (8 + 4 * (2 if kind != 1 else 4)) / K      # state + cache, read + write per K steps
+    hbm_achieved = bytes_per_su * su_per_launch / (per_launch_ms / 1e3) / 1e9
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = profiled_traffic(wl["name"])
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": (traffic * su_per_launch) if traffic else None,
+                "kernel": "split_step_kernel (fused stencil+pinning+Euler+regeneration, K-step blocked)",
+                "ops_per_site_update": ops_per_su, "crossings_per_site_update": r_cross,
+                "per_launch_ms": per_launch_ms, "site_updates_per_launch": su_per_launch,
+                "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes x {clk:.0f} MHz (median SM clock sampled "
+                              "during the timed region)",
+                "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+                        "peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+                "fused_share_of_step": st["fused_ms"] / ms if ms > 0 else None}
+
+    # ---- FP64 plain path on the same chains (the comparison the metric names) ----
+    fp64 = None
+    if args.fp64_steps > 0:
+        relax.close()
+        torch.cuda.synchronize()
+        fs = W.log_spaced_steps(args.fp64_steps, 6)
+        res = {}
+        for prec, label in ((q.FP64, "fp64"), (q.FP32_SPLIT, "split")):
+            r = q.Relaxation(wl["L"], wl["f"], wl["kind"], dt=wl["dt"], seed=wl["seed"], precision=prec,
+                             batch=wl["batch"], stream=stream)
+            if prec == q.FP32_SPLIT:
+                r.set_tuning(*tuning)
+            r.observe(fs)
+            r.reset()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                r.reset()
+                r.observe(fs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[label] = 2 * n_sites * args.fp64_steps / (e0.elapsed_time(e1) / 1e3)
+            r.close()
+        fp64 = {"value": res["fp64"], "split_same_window": res["split"], "relax_steps": args.fp64_steps,
+                "split_over_fp64": res["split"] / res["fp64"]}
+        relax = None
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        n_e2e = min(args.steps, 3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            r = q.Relaxation(wl["L"], wl["f"], wl["kind"], dt=wl["dt"], seed=wl["seed"], precision=q.FP32_SPLIT,
+                             batch=wl["batch"], stream=stream)
+            r.set_tuning(*tuning)
+            out = r.observe(sched)
+            r.close()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        h2d = sched.nbytes + wl["batch"] * (8 + 8 + 4)
+        d2h = len(sched) * wl["batch"] * 4 * 8
+        e2e = {"value": n_sites * args.relax_steps * n_e2e / wall, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": n_e2e,
+               "includes": "handle creation (device allocation + flat-start init), relaxation with fused "
+                           "observations, copy of the observables to host memory, destruction"}
+        assert np.all(np.isfinite(out["v"]))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(wl, 1 << 20, 24)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "L": wl["L"], "batch_per_gpu": wl["batch"], "kind": kind,
+                       "f": wl["f"], "dt": wl["dt"], "relax_steps": args.relax_steps,
+                       "observations": int(len(sched)), "precision": "int32 cell + f32 offset, f64 reductions",
+                       "tuning": {"tile_w": tile_w, "K": K, "tiles_per_cta": tpc},
+                       "l2": "inputs larger than L2 (4 GiB state), no flush",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "roofline": roofline, "fp64_path": fp64, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": st["launches"], "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

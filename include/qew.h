@@ -1,0 +1,193 @@
+/*
+ * qew.h -- C ABI of the GB300 (sm_103a) engine for the explicit-Euler relaxation of the
+ * discretised 1D quenched Edwards-Wilkinson equation (Ferrero, Bustingorry, Kolton,
+ * arXiv:1211.7275).
+ *
+ * The method (Sec. II and Sec. III.B of the paper): each chain s is a periodic line of L sites
+ * with a continuous displacement u_i, started flat (u_i = 0, Sec. II) and integrated with
+ * the explicit Euler method,
+ *     u_i <- u_i + dt (u_{i+1} + u_{i-1} - 2 u_i + f + F_p(i, u_i))       (Eq. 1, eta = c = 1)
+ * all forces taken from the old state.  The pinning force is built from random numbers drawn
+ * at the integer points (i, n) of the (x, u) plane and interpolated in u (Sec. III.B):
+ *     QEW_RF_GAUSS_LINEAR        F_p = (1 - d) R(i, n) + d R(i, n + 1),  R ~ N(0, 1)
+ *     QEW_RB_UNIFORM_CATMULLROM  F_p = -dV/du, V the Catmull-Rom spline through
+ *                                V(i, n - 1 .. n + 2),  V ~ U(-1, 1)
+ *     QEW_NONE                   F_p = 0 (disorder-free line)
+ * with n = floor(u), d = u - n.  The random numbers come from Philox4x32-10 (Salmon et al.,
+ * SC'11) with key (lo32(seed), hi32(seed)) and counter (i, (uint32) n, s, tag), tag 0 for R
+ * and 1 for V, regenerated on the device whenever a site changes cell (the "memory-free"
+ * disorder of Sec. IV.D).  Observables (Eqs. 3-5), per chain: v = f + (1/L) sum_i F_p(i, u_i)
+ * (the mean velocity, since the periodic Laplacian sums to zero), ubar = (1/L) sum_i u_i and
+ * w2 = (1/L) sum_i (u_i - ubar)^2.
+ *
+ * Conventions for every entry point:
+ *  - Return value: QEW_OK (0) or a negative QEW_E* status; no call aborts the process.  After
+ *    an error, qew_last_error(h) describes it (for creation errors, qew_last_error(NULL)).
+ *  - Pointers named *_out / *_in / steps / L / f / kind are HOST pointers owned by the caller;
+ *    the library copies what it needs before returning.  Device memory is owned by the handle
+ *    and freed by qew_destroy.
+ *  - Calls on one handle must not run concurrently from several host threads.
+ *  - Work is issued on the handle's stream (default: the legacy default stream, or the one set
+ *    by qew_set_stream); calls that return host data synchronise that stream.
+ *  - Time: after k Euler steps the chains are at t = k dt.  "step" always counts Euler steps
+ *    since the flat start (or since the last qew_set_state/qew_reset).
+ */
+#ifndef QEW_H
+#define QEW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qew_ctx* qew_handle;
+
+enum qew_status {
+    QEW_OK = 0,
+    QEW_EINVAL = -1,     /* invalid argument (message says which) */
+    QEW_ENOMEM = -2,     /* device or host allocation failed */
+    QEW_ECUDA = -3,      /* a CUDA call failed (message carries cudaGetErrorString) */
+    QEW_ETIMEOUT = -4,   /* reserved: a bounded device wait gave up */
+    QEW_ENONFINITE = -5, /* an observable came out NaN or infinite */
+    QEW_ESTATE = -6      /* call not allowed in the handle's current state */
+};
+
+enum qew_disorder {
+    QEW_RF_GAUSS_LINEAR = 0,
+    QEW_RB_UNIFORM_CATMULLROM = 1,
+    QEW_NONE = 2
+};
+
+enum qew_precision {
+    QEW_FP32_SPLIT = 0, /* int32 cell n + FP32 offset d in [0,1); fused, temporally blocked */
+    QEW_FP64 = 1        /* plain FP64 state, one launch per Euler step */
+};
+
+/*
+ * qew_create -- `batch` chains of `L` sites, samples s = 0 .. batch-1, all with drive `f` and
+ * disorder `disorder_kind`, time step `dt`, flat start, precision QEW_FP32_SPLIT.
+ * Requirements: 1 <= L < 2^31, batch >= 1, L * batch < 2^40, 0 < dt < 0.5, f finite.
+ * Allocates the state on the current CUDA device (QEW_ENOMEM if it does not fit).
+ * On success *out receives the handle; on failure *out is set to NULL.
+ */
+int qew_create(qew_handle* out, int64_t L, int32_t batch, double f, double dt, int32_t disorder_kind,
+               uint64_t seed);
+
+/*
+ * qew_create_batch -- `n_chains` chains of uneven lengths L[c], each with its own drive f[c]
+ * and disorder kind[c]; chain c uses sample index s = c.  `precision` is a qew_precision.
+ * Same limits per chain as qew_create; sum of L[c] < 2^40.
+ */
+int qew_create_batch(qew_handle* out, int32_t n_chains, const int64_t* L, const double* f,
+                     const int32_t* kind, double dt, uint64_t seed, int32_t precision);
+
+/* qew_set_precision -- switch between QEW_FP32_SPLIT and QEW_FP64.  Allowed only before the
+ * first Euler step (QEW_ESTATE otherwise); resets the handle to the flat start. */
+int qew_set_precision(qew_handle h, int32_t precision);
+
+/* qew_set_stream -- issue all further work on `stream` (a cudaStream_t owned by the caller,
+ * e.g. torch.cuda.current_stream().cuda_stream); NULL selects the legacy default stream.
+ * Drops any captured CUDA graphs. */
+int qew_set_stream(qew_handle h, void* stream);
+
+/*
+ * qew_set_tuning -- launch shape of the fused FP32-split kernel: `tile_w` sites per warp tile
+ * (one of 256, 512, 768, 1024), `K` Euler steps per HBM round trip (temporal-block depth,
+ * 1 <= K <= tile_w / 4), `tiles_per_cta` warp tiles per thread block (1, 2, 4 or 8).
+ * Passing 0 for all three asks for the autotuner, which times candidate shapes on the
+ * handle's own chains at the next qew_advance/qew_observe without changing their state.
+ * Results never depend on the shape beyond FP32 rounding order, which is identical: each
+ * site's arithmetic is the same for every shape.
+ */
+int qew_set_tuning(qew_handle h, int32_t tile_w, int32_t K, int32_t tiles_per_cta);
+
+/* qew_get_tuning -- the shape in use (after autotuning, the one it picked). */
+int qew_get_tuning(qew_handle h, int32_t* tile_w, int32_t* K, int32_t* tiles_per_cta);
+
+/* qew_advance -- n_steps >= 0 Euler steps of every chain. */
+int qew_advance(qew_handle h, int64_t n_steps);
+
+/*
+ * qew_observe -- advance through the observation steps `steps[0..n_times)` (strictly
+ * increasing, steps[0] >= the current step) and record at each the per-chain observables of
+ * Eqs. 3-5, fused into the integration: v_out[k * n_chains + c] = v and
+ * w2_out[k * n_chains + c] = w2 of chain c at step steps[k].  Either output may be NULL.
+ * n_times == 0 is a no-op.  Returns after the results are in host memory.  On return the
+ * chains are at step steps[n_times - 1].  QEW_ENONFINITE if an observable is NaN/Inf (the
+ * outputs are still written).
+ */
+int qew_observe(qew_handle h, const int64_t* steps, int32_t n_times, double* v_out, double* w2_out);
+
+/* qew_observe_ex -- as qew_observe, also writing the centre of mass ubar (Eq. 4). */
+int qew_observe_ex(qew_handle h, const int64_t* steps, int32_t n_times, double* v_out, double* ubar_out,
+                   double* w2_out);
+
+/*
+ * qew_get_state -- copy the displacement field to the host as FP64: u_out holds the chains one
+ * after another (chain c at offset sum_{c'<c} L[c']); *step_out (if not NULL) receives the
+ * current step.  For QEW_FP32_SPLIT the value is (double) n + (double) d, exact.
+ */
+int qew_get_state(qew_handle h, double* u_out, int64_t* step_out);
+
+/*
+ * qew_get_cells -- copy the integer cell index n_i = floor(u_i) of every site (int32, same
+ * layout as qew_get_state).  For QEW_FP64 it is floor of the FP64 state.
+ */
+int qew_get_cells(qew_handle h, int32_t* cells_out);
+
+/*
+ * qew_set_state -- replace the displacement field (FP64, layout of qew_get_state) and set the
+ * step counter to 0.  Values must be finite with |u| < 2^30.  The disorder caches are
+ * regenerated for the new cells.
+ */
+int qew_set_state(qew_handle h, const double* u_in);
+
+/* qew_reset -- back to the flat start u = 0 at step 0. */
+int qew_reset(qew_handle h);
+
+/* qew_num_sites -- total number of sites (sum of the chain lengths). */
+int qew_num_sites(qew_handle h, int64_t* n_sites);
+
+/*
+ * qew_disorder_values -- the device generator's disorder values, for validation: for each
+ * k < count, out[k] = R(s, i[k], n[k]) (kind QEW_RF_GAUSS_LINEAR) or V(s, i[k], n[k])
+ * (QEW_RB_UNIFORM_CATMULLROM), computed on the current device in the arithmetic of
+ * `precision` (FP32 values are widened to double).  Host pointers; synchronous.
+ */
+int qew_disorder_values(int32_t kind, int32_t precision, uint64_t seed, uint32_t s, const int64_t* i,
+                        const int64_t* n, int64_t count, double* out);
+
+/*
+ * qew_philox_words -- the device Philox4x32-10 block function: out[4k..4k+4) = Philox(ctr
+ * [4k..4k+4), key [2k..2k+2)) for k < n_blocks, on the current device.  Host pointers.
+ */
+int qew_philox_words(const uint32_t* ctr, const uint32_t* key, int64_t n_blocks, uint32_t* out);
+
+/*
+ * qew_enable_stats -- with enable != 0, bracket every launch of the fused FP32-split kernel with
+ * CUDA events on the handle's stream and count cell crossings; 0 turns this off.  Counters
+ * start from zero.
+ * qew_get_stats -- synchronise the handle's stream and report, since the last reset: all kernel
+ * launches issued by the handle (`launches`), launches of the fused kernel (`fused_launches`),
+ * their summed event-timed duration in ms (`fused_ms`, 0 unless stats are enabled), the
+ * site-updates they performed (`site_updates`: owned sites x Euler steps) and the cell
+ * crossings among them (`crossings`, 0 unless stats are enabled); then reset the counters.
+ * Any output pointer may be NULL.
+ */
+int qew_enable_stats(qew_handle h, int32_t enable);
+int qew_get_stats(qew_handle h, int64_t* launches, int64_t* fused_launches, double* fused_ms, int64_t* site_updates,
+                  int64_t* crossings);
+
+/* qew_last_error -- message of the last failed call on `h` (NULL: of the last failed creation
+ * or handle-less call on this thread).  Never NULL; "" if there was no error. */
+const char* qew_last_error(qew_handle h);
+
+/* qew_destroy -- free the handle and its device memory; NULL is a no-op. */
+void qew_destroy(qew_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QEW_H */

@@ -1,0 +1,1055 @@
+// qew_capi.cu -- runtime behind the C ABI declared in include/qew.h: handle, chain and tile
+// layout, device buffers, the launch schedule of Euler segments and fused observations, the
+// autotuner, and argument checking.
+//
+// The schedule follows the protocol of arXiv:1211.7275 (Sec. II-III): chains start flat, are
+// integrated with explicit Euler steps of size dt, and are observed at chosen step counts; a
+// segment of the fused FP32-split kernel never crosses an observation step, so every
+// observation sees exactly the state after that many steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "qew.h"
+#include "qew_internal.h"
+
+using namespace qew;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr int32_t kBlockTile = 1024;   // sites per block tile (FP64 path, init, conversions)
+constexpr int64_t kMaxSites = int64_t(1) << 40;
+constexpr int kNumKinds = 3;
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard()
+    {
+        if (changed)
+            cudaSetDevice(prev);
+    }
+};
+
+struct TuneKey {
+    int64_t n_sites;
+    int32_t n_chains;
+    int32_t kinds_mask;
+    int64_t min_L, max_L;
+    bool operator<(const TuneKey& o) const
+    {
+        return std::tie(n_sites, n_chains, kinds_mask, min_L, max_L) <
+               std::tie(o.n_sites, o.n_chains, o.kinds_mask, o.min_L, o.max_L);
+    }
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, std::tuple<int, int, int>> g_tune_cache;
+
+}  // namespace
+
+struct qew_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int32_t n_chains = 0;
+    std::vector<int64_t> L;
+    std::vector<double> f;
+    std::vector<int32_t> kind;
+    std::vector<int64_t> offset;
+    double dt = 0.1;
+    uint64_t seed = 0;
+    int precision = QEW_FP32_SPLIT;
+    int64_t n_sites = 0;
+    int64_t step = 0;
+    int kinds_mask = 0;
+    int n_cache = 2;
+
+    // launch shape of the fused kernel
+    int S = 16, K = 16, tpc = 4;
+    bool autotune_pending = false;
+
+    std::vector<ChainDesc> h_chains;
+    ChainDesc* d_chains = nullptr;
+    TileDesc* d_tiles[kNumKinds] = {nullptr, nullptr, nullptr};
+    int32_t n_tiles[kNumKinds] = {0, 0, 0};
+    int32_t tile_base[kNumKinds] = {0, 0, 0};
+    int32_t w_own = 0;
+    TileDesc* d_btiles = nullptr;
+    int32_t n_btiles = 0;
+
+    SplitState sp[2] = {};
+    int cur = 0;
+    F64State f64 = {};
+    double* u64[2] = {nullptr, nullptr};
+
+    double* d_shift = nullptr;
+    double* d_partial = nullptr;
+    size_t partial_slots = 0;
+    double* d_obs = nullptr;
+    size_t obs_cap = 0;
+    double* h_obs = nullptr;
+    size_t h_obs_cap = 0;
+
+    // statistics (qew_enable_stats / qew_get_stats)
+    int64_t sites_of_kind[kNumKinds] = {0, 0, 0};
+    bool stats_on = false;
+    int64_t n_launches = 0;
+    int64_t n_fused = 0;
+    int64_t n_site_updates = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    unsigned long long* d_crossings = nullptr;
+
+    std::string err;
+};
+
+namespace {
+
+int fail(qew_ctx* h, int code, const std::string& msg)
+{
+    if (h)
+        h->err = msg;
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(qew_ctx* h, cudaError_t e, const char* where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();  // clear a sticky launch error where possible
+    return fail(h, e == cudaErrorMemoryAllocation ? QEW_ENOMEM : QEW_ECUDA, m);
+}
+
+#define QEW_CUDA(h, call, where)                     \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess)                       \
+            return cuda_fail((h), e_, (where));      \
+    } while (0)
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0)
+        return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+template <class T>
+void dev_free(T*& p)
+{
+    if (p)
+        cudaFree(p);
+    p = nullptr;
+}
+
+void free_split(qew_ctx* h)
+{
+    for (int b = 0; b < 2; ++b) {
+        dev_free(h->sp[b].cell);
+        dev_free(h->sp[b].off);
+        for (int c = 0; c < 4; ++c)
+            dev_free(h->sp[b].c[c]);
+    }
+}
+
+void free_f64(qew_ctx* h)
+{
+    dev_free(h->u64[0]);
+    dev_free(h->u64[1]);
+    dev_free(h->f64.ncache);
+    for (int c = 0; c < 4; ++c)
+        dev_free(h->f64.c[c]);
+    h->f64.u = nullptr;
+}
+
+void free_events(qew_ctx* h)
+{
+    for (cudaEvent_t e : h->ev_pool)
+        cudaEventDestroy(e);
+    h->ev_pool.clear();
+    h->ev_used = 0;
+}
+
+void free_all(qew_ctx* h)
+{
+    free_events(h);
+    dev_free(h->d_crossings);
+    free_split(h);
+    free_f64(h);
+    dev_free(h->d_chains);
+    for (int k = 0; k < kNumKinds; ++k)
+        dev_free(h->d_tiles[k]);
+    dev_free(h->d_btiles);
+    dev_free(h->d_shift);
+    dev_free(h->d_partial);
+    dev_free(h->d_obs);
+    if (h->h_obs)
+        cudaFreeHost(h->h_obs);
+    h->h_obs = nullptr;
+}
+
+int alloc_state(qew_ctx* h)
+{
+    const size_t N = static_cast<size_t>(h->n_sites);
+    if (h->precision == QEW_FP32_SPLIT) {
+        free_f64(h);
+        if (h->sp[0].cell)
+            return QEW_OK;
+        for (int b = 0; b < 2; ++b) {
+            QEW_CUDA(h, dev_alloc(&h->sp[b].cell, N), "allocating the cell array");
+            QEW_CUDA(h, dev_alloc(&h->sp[b].off, N), "allocating the offset array");
+            for (int c = 0; c < h->n_cache; ++c)
+                QEW_CUDA(h, dev_alloc(&h->sp[b].c[c], N), "allocating the disorder cache");
+        }
+    } else {
+        free_split(h);
+        if (h->u64[0])
+            return QEW_OK;
+        QEW_CUDA(h, dev_alloc(&h->u64[0], N), "allocating the FP64 state");
+        QEW_CUDA(h, dev_alloc(&h->u64[1], N), "allocating the FP64 state");
+        QEW_CUDA(h, dev_alloc(&h->f64.ncache, N), "allocating the FP64 cache cells");
+        for (int c = 0; c < h->n_cache; ++c)
+            QEW_CUDA(h, dev_alloc(&h->f64.c[c], N), "allocating the FP64 disorder cache");
+    }
+    return QEW_OK;
+}
+
+// Tile lists for the current precision and launch shape; uploads chain descriptors and sizes
+// the partial-sum buffer.
+int build_layout(qew_ctx* h)
+{
+    const int32_t tile_w = 32 * h->S;
+    h->w_own = tile_w - 2 * h->K;
+    std::vector<TileDesc> lists[kNumKinds];
+    std::vector<TileDesc> blocks;
+    h->h_chains.assign(h->n_chains, ChainDesc{});
+    std::vector<int32_t> first(h->n_chains), count(h->n_chains);
+    for (int32_t c = 0; c < h->n_chains; ++c) {
+        ChainDesc& d = h->h_chains[c];
+        d.offset = h->offset[c];
+        d.L = static_cast<int32_t>(h->L[c]);
+        d.s = static_cast<uint32_t>(c);
+        d.kind = h->kind[c];
+        d.f32 = static_cast<float>(h->f[c]);
+        d.f64 = h->f[c];
+        for (int32_t st = 0; st < d.L; st += kBlockTile)
+            blocks.push_back(TileDesc{c, st});
+        if (h->precision == QEW_FP32_SPLIT) {
+            auto& lst = lists[d.kind];
+            first[c] = static_cast<int32_t>(lst.size());
+            for (int64_t st = 0; st < d.L; st += h->w_own)
+                lst.push_back(TileDesc{c, static_cast<int32_t>(st)});
+            count[c] = static_cast<int32_t>(lst.size()) - first[c];
+        }
+    }
+    size_t slots = 0;
+    if (h->precision == QEW_FP32_SPLIT) {
+        int32_t base = 0;
+        for (int k = 0; k < kNumKinds; ++k) {
+            h->tile_base[k] = base;
+            h->n_tiles[k] = static_cast<int32_t>(lists[k].size());
+            base += h->n_tiles[k];
+        }
+        for (int32_t c = 0; c < h->n_chains; ++c) {
+            h->h_chains[c].tile0 = h->tile_base[h->kind[c]] + first[c];
+            h->h_chains[c].ntiles = count[c];
+        }
+        slots = static_cast<size_t>(base);
+    } else {
+        int32_t b = 0;
+        for (int32_t c = 0; c < h->n_chains; ++c) {
+            const int32_t nb = static_cast<int32_t>((h->L[c] + kBlockTile - 1) / kBlockTile);
+            h->h_chains[c].tile0 = b;
+            h->h_chains[c].ntiles = nb;
+            b += nb;
+        }
+        slots = static_cast<size_t>(b);
+        for (int k = 0; k < kNumKinds; ++k)
+            h->n_tiles[k] = 0;
+    }
+    dev_free(h->d_chains);
+    for (int k = 0; k < kNumKinds; ++k)
+        dev_free(h->d_tiles[k]);
+    dev_free(h->d_btiles);
+    QEW_CUDA(h, dev_alloc(&h->d_chains, h->h_chains.size()), "allocating chain descriptors");
+    QEW_CUDA(h, cudaMemcpy(h->d_chains, h->h_chains.data(), h->h_chains.size() * sizeof(ChainDesc),
+                           cudaMemcpyHostToDevice), "uploading chain descriptors");
+    for (int k = 0; k < kNumKinds; ++k) {
+        if (lists[k].empty())
+            continue;
+        QEW_CUDA(h, dev_alloc(&h->d_tiles[k], lists[k].size()), "allocating tile lists");
+        QEW_CUDA(h, cudaMemcpy(h->d_tiles[k], lists[k].data(), lists[k].size() * sizeof(TileDesc),
+                               cudaMemcpyHostToDevice), "uploading tile lists");
+    }
+    h->n_btiles = static_cast<int32_t>(blocks.size());
+    QEW_CUDA(h, dev_alloc(&h->d_btiles, blocks.size()), "allocating block tiles");
+    QEW_CUDA(h, cudaMemcpy(h->d_btiles, blocks.data(), blocks.size() * sizeof(TileDesc), cudaMemcpyHostToDevice),
+             "uploading block tiles");
+    if (slots > h->partial_slots) {
+        dev_free(h->d_partial);
+        QEW_CUDA(h, dev_alloc(&h->d_partial, slots * 3), "allocating partial sums");
+        h->partial_slots = slots;
+    }
+    return QEW_OK;
+}
+
+// Flat start (u_in == nullptr) or the given device FP64 state; step counter to 0 and the
+// reference shifts to `shift0`.
+int init_state(qew_ctx* h, const double* d_u_in, const std::vector<double>& shift0)
+{
+    h->cur = 0;
+    h->step = 0;
+    if (h->precision == QEW_FP32_SPLIT) {
+        QEW_CUDA(h, split_init(h->d_chains, h->n_chains, h->d_btiles, h->n_btiles, kBlockTile, h->sp[0], h->seed,
+                               h->kinds_mask & 2, d_u_in, h->stream), "launching the state initialisation");
+    } else {
+        h->f64.u = h->u64[0];
+        QEW_CUDA(h, f64_init(h->d_chains, h->d_btiles, h->n_btiles, kBlockTile, h->f64, h->seed, h->kinds_mask & 2,
+                             d_u_in, h->stream), "launching the FP64 state initialisation");
+    }
+    h->n_launches += 1;
+    QEW_CUDA(h, cudaMemcpyAsync(h->d_shift, shift0.data(), shift0.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                h->stream), "setting reference shifts");
+    QEW_CUDA(h, cudaStreamSynchronize(h->stream), "initialising the state");
+    return QEW_OK;
+}
+
+SplitLaunch split_args(qew_ctx* h, int kind, int K, int do_obs, SplitState in, SplitState out)
+{
+    SplitLaunch a{};
+    a.tiles = h->d_tiles[kind];
+    a.n_tiles = h->n_tiles[kind];
+    a.tile_base = h->tile_base[kind];
+    a.chains = h->d_chains;
+    a.in = in;
+    a.out = out;
+    a.K = K;
+    a.w_own = h->w_own;
+    a.dt = static_cast<float>(h->dt);
+    a.seed = h->seed;
+    a.do_obs = do_obs;
+    a.shift = h->d_shift;
+    a.partial = h->d_partial;
+    a.crossings = h->stats_on ? h->d_crossings : nullptr;
+    return a;
+}
+
+int next_event(qew_ctx* h, cudaEvent_t* ev)
+{
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e;
+        QEW_CUDA(h, cudaEventCreate(&e), "creating a timing event");
+        h->ev_pool.push_back(e);
+    }
+    *ev = h->ev_pool[h->ev_used++];
+    return QEW_OK;
+}
+
+int launch_split_all(qew_ctx* h, int K, int do_obs, SplitState in, SplitState out)
+{
+    for (int k = 0; k < kNumKinds; ++k) {
+        if (h->n_tiles[k] == 0)
+            continue;
+        const SplitLaunch a = split_args(h, k, K, do_obs, in, out);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (h->stats_on) {
+            int rc = next_event(h, &e0);
+            if (rc == QEW_OK)
+                rc = next_event(h, &e1);
+            if (rc != QEW_OK)
+                return rc;
+            QEW_CUDA(h, cudaEventRecord(e0, h->stream), "recording a timing event");
+        }
+        QEW_CUDA(h, split_step(k, h->S, h->tpc, a, h->stream), "launching the fused step kernel");
+        if (h->stats_on)
+            QEW_CUDA(h, cudaEventRecord(e1, h->stream), "recording a timing event");
+        h->n_launches += 1;
+        h->n_fused += 1;
+        h->n_site_updates += h->sites_of_kind[k] * K;
+    }
+    return QEW_OK;
+}
+
+F64Launch f64_args(qew_ctx* h)
+{
+    F64Launch a{};
+    a.tiles = h->d_btiles;
+    a.n_tiles = h->n_btiles;
+    a.w_tile = kBlockTile;
+    a.chains = h->d_chains;
+    a.st = h->f64;
+    a.u_in = h->u64[h->cur];
+    a.u_out = h->u64[h->cur ^ 1];
+    a.dt = h->dt;
+    a.seed = h->seed;
+    a.shift = h->d_shift;
+    a.partial = h->d_partial;
+    return a;
+}
+
+int autotune(qew_ctx* h);
+
+// Advance to `target` (>= current step); with `obs` record the observables there into obs.
+int run_to(qew_ctx* h, int64_t target, double* obs)
+{
+    if (h->precision == QEW_FP32_SPLIT) {
+        if (h->autotune_pending) {
+            int rc = autotune(h);
+            if (rc != QEW_OK)
+                return rc;
+        }
+        bool observed = false;
+        while (h->step < target) {
+            const int Keff = static_cast<int>(std::min<int64_t>(h->K, target - h->step));
+            const bool last = (h->step + Keff == target);
+            const int do_obs = (obs != nullptr && last) ? 1 : 0;
+            int rc = launch_split_all(h, Keff, do_obs, h->sp[h->cur], h->sp[h->cur ^ 1]);
+            if (rc != QEW_OK)
+                return rc;
+            h->cur ^= 1;
+            h->step += Keff;
+            observed = observed || do_obs;
+        }
+        if (obs && !observed) {
+            int rc = launch_split_all(h, 0, 1, h->sp[h->cur], h->sp[h->cur ^ 1]);
+            if (rc != QEW_OK)
+                return rc;
+        }
+        if (obs) {
+            QEW_CUDA(h, reduce_chains(h->d_chains, h->n_chains, h->d_partial, h->d_shift, obs, 1, h->stream),
+                     "launching the observable reduction");
+            h->n_launches += 1;
+        }
+    } else {
+        while (h->step < target) {
+            QEW_CUDA(h, f64_step(f64_args(h), h->stream), "launching the FP64 step kernel");
+            h->cur ^= 1;
+            h->f64.u = h->u64[h->cur];
+            ++h->step;
+            h->n_launches += 1;
+            h->n_site_updates += h->n_sites;
+        }
+        if (obs) {
+            QEW_CUDA(h, f64_observe(f64_args(h), h->stream), "launching the FP64 observation kernel");
+            QEW_CUDA(h, reduce_chains(h->d_chains, h->n_chains, h->d_partial, h->d_shift, obs, 1, h->stream),
+                     "launching the observable reduction");
+            h->n_launches += 2;
+        }
+    }
+    return QEW_OK;
+}
+
+// Times candidate launch shapes on the handle's own chains: each trial launch reads the
+// current state and writes the other ping-pong buffer, so the state is unchanged.
+int autotune(qew_ctx* h)
+{
+    h->autotune_pending = false;
+    TuneKey key{h->n_sites, h->n_chains, h->kinds_mask,
+                *std::min_element(h->L.begin(), h->L.end()), *std::max_element(h->L.begin(), h->L.end())};
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            std::tie(h->S, h->K, h->tpc) = it->second;
+            return build_layout(h);
+        }
+    }
+    const int S_all[] = {8, 16, 24, 32};
+    const int K_all[] = {8, 16, 32};
+    const int T_all[] = {2, 4};
+    float best = 1e30f;
+    int bS = h->S, bK = h->K, bT = h->tpc;
+    cudaEvent_t e0, e1;
+    QEW_CUDA(h, cudaEventCreate(&e0), "creating tuning events");
+    QEW_CUDA(h, cudaEventCreate(&e1), "creating tuning events");
+    for (int S : S_all) {
+        bool ok = true;
+        for (int k = 0; k < kNumKinds; ++k)
+            if ((h->kinds_mask >> k & 1) && !split_supported(k, S))
+                ok = false;
+        if (!ok)
+            continue;
+        for (int K : K_all) {
+            if (4 * K > 32 * S)
+                continue;
+            for (int T : T_all) {
+                if (split_smem_bytes((h->kinds_mask & 2) ? kRB : kRF, S, T) > 200 * 1024)
+                    continue;
+                h->S = S;
+                h->K = K;
+                h->tpc = T;
+                int rc = build_layout(h);
+                if (rc != QEW_OK)
+                    return rc;
+                float ms_best = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    cudaEventRecord(e0, h->stream);
+                    rc = launch_split_all(h, K, 0, h->sp[h->cur], h->sp[h->cur ^ 1]);
+                    if (rc != QEW_OK)
+                        return rc;
+                    cudaEventRecord(e1, h->stream);
+                    QEW_CUDA(h, cudaEventSynchronize(e1), "timing a tuning candidate");
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0)
+                        ms_best = std::min(ms_best, ms);
+                }
+                const float per = ms_best / static_cast<float>(K);
+                if (per < best) {
+                    best = per;
+                    bS = S;
+                    bK = K;
+                    bT = T;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->S = bS;
+    h->K = bK;
+    h->tpc = bT;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[key] = std::make_tuple(bS, bK, bT);
+    }
+    return build_layout(h);
+}
+
+int validate_common(double dt, uint64_t)
+{
+    if (!(dt > 0.0 && dt < 0.5))
+        return fail(nullptr, QEW_EINVAL, "dt must lie in (0, 0.5)");
+    return QEW_OK;
+}
+
+int create_impl(qew_handle* out, int32_t n_chains, const int64_t* L, const double* f, const int32_t* kind, double dt,
+                uint64_t seed, int32_t precision)
+{
+    if (!out)
+        return fail(nullptr, QEW_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    if (n_chains < 1)
+        return fail(nullptr, QEW_EINVAL, "need at least one chain");
+    if (!L || !f || !kind)
+        return fail(nullptr, QEW_EINVAL, "L, f and kind must not be NULL");
+    int rc = validate_common(dt, seed);
+    if (rc != QEW_OK)
+        return rc;
+    if (precision != QEW_FP32_SPLIT && precision != QEW_FP64)
+        return fail(nullptr, QEW_EINVAL, "precision must be QEW_FP32_SPLIT or QEW_FP64");
+    int64_t total = 0;
+    for (int32_t c = 0; c < n_chains; ++c) {
+        if (L[c] < 1 || L[c] >= (int64_t(1) << 31))
+            return fail(nullptr, QEW_EINVAL, "chain length " + std::to_string(L[c]) + " outside [1, 2^31)");
+        if (!std::isfinite(f[c]))
+            return fail(nullptr, QEW_EINVAL, "drive f must be finite");
+        if (kind[c] < QEW_RF_GAUSS_LINEAR || kind[c] > QEW_NONE)
+            return fail(nullptr, QEW_EINVAL, "unknown disorder kind " + std::to_string(kind[c]));
+        total += L[c];
+        if (total >= kMaxSites)
+            return fail(nullptr, QEW_EINVAL, "total number of sites must be below 2^40");
+    }
+    qew_ctx* h = new (std::nothrow) qew_ctx();
+    if (!h)
+        return fail(nullptr, QEW_ENOMEM, "host allocation of the handle failed");
+    try {
+        cudaGetDevice(&h->device);
+        h->n_chains = n_chains;
+        h->L.assign(L, L + n_chains);
+        h->f.assign(f, f + n_chains);
+        h->kind.assign(kind, kind + n_chains);
+        h->offset.resize(n_chains);
+        int64_t off = 0;
+        for (int32_t c = 0; c < n_chains; ++c) {
+            h->offset[c] = off;
+            off += L[c];
+            h->kinds_mask |= 1 << kind[c];
+            h->sites_of_kind[kind[c]] += L[c];
+        }
+        h->n_sites = off;
+        h->n_cache = (h->kinds_mask & 2) ? 4 : 2;
+        h->dt = dt;
+        h->seed = seed;
+        h->precision = precision;
+        if (h->kinds_mask & 2)
+            h->S = 8;
+        rc = build_layout(h);
+        if (rc == QEW_OK)
+            rc = alloc_state(h);
+        if (rc == QEW_OK) {
+            cudaError_t e = dev_alloc(&h->d_shift, static_cast<size_t>(n_chains));
+            if (e != cudaSuccess)
+                rc = cuda_fail(h, e, "allocating reference shifts");
+        }
+        if (rc == QEW_OK)
+            rc = init_state(h, nullptr, std::vector<double>(n_chains, 0.0));
+    } catch (const std::bad_alloc&) {
+        rc = fail(h, QEW_ENOMEM, "host allocation failed");
+    }
+    if (rc != QEW_OK) {
+        g_last_error = h->err;
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return QEW_OK;
+}
+
+int check_handle(qew_handle h)
+{
+    if (!h)
+        return fail(nullptr, QEW_EINVAL, "handle must not be NULL");
+    return QEW_OK;
+}
+
+int ensure_obs(qew_ctx* h, size_t n)
+{
+    if (n > h->obs_cap) {
+        dev_free(h->d_obs);
+        QEW_CUDA(h, dev_alloc(&h->d_obs, n), "allocating observation buffer");
+        h->obs_cap = n;
+    }
+    if (n > h->h_obs_cap) {
+        if (h->h_obs)
+            cudaFreeHost(h->h_obs);
+        h->h_obs = nullptr;
+        QEW_CUDA(h, cudaMallocHost(reinterpret_cast<void**>(&h->h_obs), n * sizeof(double)),
+                 "allocating pinned observation buffer");
+        h->h_obs_cap = n;
+    }
+    return QEW_OK;
+}
+
+int observe_impl(qew_ctx* h, const int64_t* steps, int32_t n_times, double* v_out, double* ubar_out,
+                 double* w2_out)
+{
+    if (n_times < 0)
+        return fail(h, QEW_EINVAL, "n_times must be >= 0");
+    if (n_times == 0)
+        return QEW_OK;
+    if (!steps)
+        return fail(h, QEW_EINVAL, "steps must not be NULL");
+    if (steps[0] < h->step)
+        return fail(h, QEW_EINVAL, "steps[0] = " + std::to_string(steps[0]) + " lies before the current step " +
+                                       std::to_string(h->step));
+    for (int32_t k = 1; k < n_times; ++k)
+        if (steps[k] <= steps[k - 1])
+            return fail(h, QEW_EINVAL, "steps must be strictly increasing");
+    const size_t per = static_cast<size_t>(h->n_chains) * 4;
+    int rc = ensure_obs(h, per * n_times);
+    if (rc != QEW_OK)
+        return rc;
+    for (int32_t k = 0; k < n_times; ++k) {
+        rc = run_to(h, steps[k], h->d_obs + per * k);
+        if (rc != QEW_OK)
+            return rc;
+    }
+    QEW_CUDA(h, cudaMemcpyAsync(h->h_obs, h->d_obs, per * n_times * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->stream), "copying observables to the host");
+    QEW_CUDA(h, cudaStreamSynchronize(h->stream), "running the relaxation");
+    bool finite = true;
+    for (int32_t k = 0; k < n_times; ++k) {
+        for (int32_t c = 0; c < h->n_chains; ++c) {
+            const double* o = h->h_obs + per * k + 4 * c;
+            const double Ld = static_cast<double>(h->L[c]);
+            const double m1 = o[1] / Ld;
+            const double v = h->f[c] + o[0] / Ld;
+            const double ub = o[3] + m1;
+            const double w2 = o[2] / Ld - m1 * m1;
+            const size_t idx = static_cast<size_t>(k) * h->n_chains + c;
+            if (v_out)
+                v_out[idx] = v;
+            if (ubar_out)
+                ubar_out[idx] = ub;
+            if (w2_out)
+                w2_out[idx] = w2;
+            finite = finite && std::isfinite(v) && std::isfinite(ub) && std::isfinite(w2);
+        }
+    }
+    if (!finite)
+        return fail(h, QEW_ENONFINITE, "an observable is not finite");
+    return QEW_OK;
+}
+
+int get_state_impl(qew_ctx* h, double* u_out, int32_t* cells_out, int64_t* step_out)
+{
+    const size_t N = static_cast<size_t>(h->n_sites);
+    if (step_out)
+        *step_out = h->step;
+    if (!u_out && !cells_out)
+        return QEW_OK;
+    double* d_u = nullptr;
+    int32_t* d_c = nullptr;
+    int rc = QEW_OK;
+    cudaError_t e = cudaSuccess;
+    if (u_out && h->precision == QEW_FP32_SPLIT)
+        e = dev_alloc(&d_u, N);
+    if (e == cudaSuccess && cells_out)
+        e = dev_alloc(&d_c, N);
+    if (e != cudaSuccess) {
+        rc = cuda_fail(h, e, "allocating a state copy");
+    } else if (h->precision == QEW_FP32_SPLIT) {
+        e = split_to_f64(h->d_chains, h->d_btiles, h->n_btiles, kBlockTile, h->sp[h->cur], d_u, d_c, h->stream);
+        if (e == cudaSuccess && u_out)
+            e = cudaMemcpyAsync(u_out, d_u, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    } else {
+        if (cells_out)
+            e = f64_cells(h->d_chains, h->d_btiles, h->n_btiles, kBlockTile, h->u64[h->cur], d_c, h->stream);
+        if (e == cudaSuccess && u_out)
+            e = cudaMemcpyAsync(u_out, h->u64[h->cur], N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    }
+    if (rc == QEW_OK && e == cudaSuccess && cells_out)
+        e = cudaMemcpyAsync(cells_out, d_c, N * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (rc == QEW_OK && e == cudaSuccess)
+        e = cudaStreamSynchronize(h->stream);
+    if (rc == QEW_OK && e != cudaSuccess)
+        rc = cuda_fail(h, e, "reading the state");
+    dev_free(d_u);
+    dev_free(d_c);
+    return rc;
+}
+
+int set_state_impl(qew_ctx* h, const double* u_in)
+{
+    const size_t N = static_cast<size_t>(h->n_sites);
+    std::vector<double> shift0(h->n_chains, 0.0);
+    for (int32_t c = 0; c < h->n_chains; ++c) {
+        double acc = 0.0;
+        for (int64_t i = 0; i < h->L[c]; ++i) {
+            const double u = u_in[h->offset[c] + i];
+            if (!std::isfinite(u) || std::fabs(u) >= 1073741824.0)
+                return fail(h, QEW_EINVAL, "state values must be finite with |u| < 2^30");
+            acc += u;
+        }
+        shift0[c] = std::floor(acc / static_cast<double>(h->L[c]) + 0.5);
+    }
+    double* d_u = nullptr;
+    cudaError_t e = dev_alloc(&d_u, N);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "allocating a state copy");
+    e = cudaMemcpy(d_u, u_in, N * sizeof(double), cudaMemcpyHostToDevice);
+    int rc = (e == cudaSuccess) ? init_state(h, d_u, shift0) : cuda_fail(h, e, "uploading the state");
+    dev_free(d_u);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qew_create(qew_handle* out, int64_t L, int32_t batch, double f, double dt, int32_t disorder_kind, uint64_t seed)
+{
+    if (batch < 1)
+        return fail(nullptr, QEW_EINVAL, "batch must be >= 1");
+    try {
+        std::vector<int64_t> Ls(batch, L);
+        std::vector<double> fs(batch, f);
+        std::vector<int32_t> ks(batch, disorder_kind);
+        return create_impl(out, batch, Ls.data(), fs.data(), ks.data(), dt, seed, QEW_FP32_SPLIT);
+    } catch (const std::bad_alloc&) {
+        return fail(nullptr, QEW_ENOMEM, "host allocation failed");
+    }
+}
+
+int qew_create_batch(qew_handle* out, int32_t n_chains, const int64_t* L, const double* f, const int32_t* kind,
+                     double dt, uint64_t seed, int32_t precision)
+{
+    return create_impl(out, n_chains, L, f, kind, dt, seed, precision);
+}
+
+int qew_set_precision(qew_handle h, int32_t precision)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    if (precision != QEW_FP32_SPLIT && precision != QEW_FP64)
+        return fail(h, QEW_EINVAL, "precision must be QEW_FP32_SPLIT or QEW_FP64");
+    if (h->step != 0)
+        return fail(h, QEW_ESTATE, "precision can only change before the first step");
+    DeviceGuard g(h->device);
+    h->precision = precision;
+    int rc = build_layout(h);
+    if (rc == QEW_OK)
+        rc = alloc_state(h);
+    if (rc == QEW_OK)
+        rc = init_state(h, nullptr, std::vector<double>(h->n_chains, 0.0));
+    return rc;
+}
+
+int qew_set_stream(qew_handle h, void* stream)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return QEW_OK;
+}
+
+int qew_set_tuning(qew_handle h, int32_t tile_w, int32_t K, int32_t tiles_per_cta)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    DeviceGuard g(h->device);
+    if (tile_w == 0 && K == 0 && tiles_per_cta == 0) {
+        h->autotune_pending = true;
+        return QEW_OK;
+    }
+    if (tile_w % 32 != 0)
+        return fail(h, QEW_EINVAL, "tile_w must be a multiple of 32");
+    const int S = tile_w / 32;
+    for (int k = 0; k < kNumKinds; ++k)
+        if ((h->kinds_mask >> k & 1) && !split_supported(k, S))
+            return fail(h, QEW_EINVAL, "tile_w " + std::to_string(tile_w) + " is not supported for this disorder kind");
+    if (K < 1 || 4 * K > tile_w)
+        return fail(h, QEW_EINVAL, "K must lie in [1, tile_w / 4]");
+    if (tiles_per_cta != 1 && tiles_per_cta != 2 && tiles_per_cta != 4 && tiles_per_cta != 8)
+        return fail(h, QEW_EINVAL, "tiles_per_cta must be 1, 2, 4 or 8");
+    if (split_smem_bytes((h->kinds_mask & 2) ? kRB : kRF, S, tiles_per_cta) > 227 * 1024)
+        return fail(h, QEW_EINVAL, "tile_w * tiles_per_cta needs more shared memory than a block has");
+    h->S = S;
+    h->K = K;
+    h->tpc = tiles_per_cta;
+    h->autotune_pending = false;
+    return build_layout(h);
+}
+
+int qew_get_tuning(qew_handle h, int32_t* tile_w, int32_t* K, int32_t* tiles_per_cta)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    if (tile_w)
+        *tile_w = 32 * h->S;
+    if (K)
+        *K = h->K;
+    if (tiles_per_cta)
+        *tiles_per_cta = h->tpc;
+    return QEW_OK;
+}
+
+int qew_advance(qew_handle h, int64_t n_steps)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    if (n_steps < 0)
+        return fail(h, QEW_EINVAL, "n_steps must be >= 0");
+    DeviceGuard g(h->device);
+    int rc = run_to(h, h->step + n_steps, nullptr);
+    if (rc == QEW_OK) {
+        cudaError_t e = cudaPeekAtLastError();
+        if (e != cudaSuccess)
+            return cuda_fail(h, e, "advancing");
+    }
+    return rc;
+}
+
+int qew_observe(qew_handle h, const int64_t* steps, int32_t n_times, double* v_out, double* w2_out)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    DeviceGuard g(h->device);
+    return observe_impl(h, steps, n_times, v_out, nullptr, w2_out);
+}
+
+int qew_observe_ex(qew_handle h, const int64_t* steps, int32_t n_times, double* v_out, double* ubar_out,
+                   double* w2_out)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    DeviceGuard g(h->device);
+    return observe_impl(h, steps, n_times, v_out, ubar_out, w2_out);
+}
+
+int qew_get_state(qew_handle h, double* u_out, int64_t* step_out)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    DeviceGuard g(h->device);
+    return get_state_impl(h, u_out, nullptr, step_out);
+}
+
+int qew_get_cells(qew_handle h, int32_t* cells_out)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    if (!cells_out)
+        return fail(h, QEW_EINVAL, "cells_out must not be NULL");
+    DeviceGuard g(h->device);
+    return get_state_impl(h, nullptr, cells_out, nullptr);
+}
+
+int qew_set_state(qew_handle h, const double* u_in)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    if (!u_in)
+        return fail(h, QEW_EINVAL, "u_in must not be NULL");
+    DeviceGuard g(h->device);
+    return set_state_impl(h, u_in);
+}
+
+int qew_reset(qew_handle h)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    DeviceGuard g(h->device);
+    return init_state(h, nullptr, std::vector<double>(h->n_chains, 0.0));
+}
+
+int qew_num_sites(qew_handle h, int64_t* n_sites)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    if (!n_sites)
+        return fail(h, QEW_EINVAL, "n_sites must not be NULL");
+    *n_sites = h->n_sites;
+    return QEW_OK;
+}
+
+int qew_disorder_values(int32_t kind, int32_t precision, uint64_t seed, uint32_t s, const int64_t* i,
+                        const int64_t* n, int64_t count, double* out)
+{
+    if (kind != QEW_RF_GAUSS_LINEAR && kind != QEW_RB_UNIFORM_CATMULLROM)
+        return fail(nullptr, QEW_EINVAL, "kind must be QEW_RF_GAUSS_LINEAR or QEW_RB_UNIFORM_CATMULLROM");
+    if (precision != QEW_FP32_SPLIT && precision != QEW_FP64)
+        return fail(nullptr, QEW_EINVAL, "unknown precision");
+    if (count < 0 || (count > 0 && (!i || !n || !out)))
+        return fail(nullptr, QEW_EINVAL, "bad count or NULL array");
+    if (count == 0)
+        return QEW_OK;
+    int64_t *di = nullptr, *dn = nullptr;
+    double* dout = nullptr;
+    cudaError_t e = dev_alloc(&di, count);
+    if (e == cudaSuccess)
+        e = dev_alloc(&dn, count);
+    if (e == cudaSuccess)
+        e = dev_alloc(&dout, count);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(di, i, count * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dn, n, count * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = disorder_values(kind, precision == QEW_FP64, seed, s, di, dn, count, dout, nullptr);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, dout, count * sizeof(double), cudaMemcpyDeviceToHost);
+    dev_free(di);
+    dev_free(dn);
+    dev_free(dout);
+    if (e != cudaSuccess)
+        return cuda_fail(nullptr, e, "qew_disorder_values");
+    return QEW_OK;
+}
+
+int qew_philox_words(const uint32_t* ctr, const uint32_t* key, int64_t n_blocks, uint32_t* out)
+{
+    if (n_blocks < 0 || (n_blocks > 0 && (!ctr || !key || !out)))
+        return fail(nullptr, QEW_EINVAL, "bad count or NULL array");
+    if (n_blocks == 0)
+        return QEW_OK;
+    uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr;
+    cudaError_t e = dev_alloc(&dc, 4 * n_blocks);
+    if (e == cudaSuccess)
+        e = dev_alloc(&dk, 2 * n_blocks);
+    if (e == cudaSuccess)
+        e = dev_alloc(&dout, 4 * n_blocks);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dc, ctr, 16 * n_blocks, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dk, key, 8 * n_blocks, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = philox_words(dc, dk, n_blocks, dout, nullptr);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, dout, 16 * n_blocks, cudaMemcpyDeviceToHost);
+    dev_free(dc);
+    dev_free(dk);
+    dev_free(dout);
+    if (e != cudaSuccess)
+        return cuda_fail(nullptr, e, "qew_philox_words");
+    return QEW_OK;
+}
+
+int qew_enable_stats(qew_handle h, int32_t enable)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    DeviceGuard g(h->device);
+    QEW_CUDA(h, cudaStreamSynchronize(h->stream), "synchronising before enabling stats");
+    if (enable && !h->d_crossings)
+        QEW_CUDA(h, dev_alloc(&h->d_crossings, 1), "allocating the crossing counter");
+    if (h->d_crossings)
+        QEW_CUDA(h, cudaMemset(h->d_crossings, 0, sizeof(unsigned long long)), "clearing the crossing counter");
+    h->stats_on = enable != 0;
+    h->n_launches = h->n_fused = h->n_site_updates = 0;
+    h->ev_used = 0;
+    return QEW_OK;
+}
+
+int qew_get_stats(qew_handle h, int64_t* launches, int64_t* fused_launches, double* fused_ms, int64_t* site_updates,
+                  int64_t* crossings)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    DeviceGuard g(h->device);
+    QEW_CUDA(h, cudaStreamSynchronize(h->stream), "synchronising for stats");
+    double ms = 0.0;
+    for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+        float t = 0.0f;
+        QEW_CUDA(h, cudaEventElapsedTime(&t, h->ev_pool[k], h->ev_pool[k + 1]), "reading a timing event");
+        ms += t;
+    }
+    unsigned long long cr = 0;
+    if (h->stats_on && h->d_crossings) {
+        QEW_CUDA(h, cudaMemcpy(&cr, h->d_crossings, sizeof(cr), cudaMemcpyDeviceToHost), "reading crossings");
+        QEW_CUDA(h, cudaMemset(h->d_crossings, 0, sizeof(cr)), "clearing the crossing counter");
+    }
+    if (launches)
+        *launches = h->n_launches;
+    if (fused_launches)
+        *fused_launches = h->n_fused;
+    if (fused_ms)
+        *fused_ms = ms;
+    if (site_updates)
+        *site_updates = h->n_site_updates;
+    if (crossings)
+        *crossings = static_cast<int64_t>(cr);
+    h->n_launches = h->n_fused = h->n_site_updates = 0;
+    h->ev_used = 0;
+    return QEW_OK;
+}
+
+const char* qew_last_error(qew_handle h)
+{
+    return h ? h->err.c_str() : g_last_error.c_str();
+}
+
+void qew_destroy(qew_handle h)
+{
+    if (!h)
+        return;
+    {
+        DeviceGuard g(h->device);
+        cudaStreamSynchronize(h->stream);
+        free_all(h);
+    }
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// qew_device.cuh -- device-side building blocks of the qEW engine: the Philox4x32-10 block
+// function, the transforms of its output words to disorder values, and the descriptors that
+// map warp tiles to chains.
+//
+// Disorder (arXiv:1211.7275, Sec. III.B): uncorrelated random numbers drawn at the integer
+// points (i, n) of the (x, u) plane, generated on demand (the memory-free variant of
+// Sec. IV.D).  The generator is Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), keyed by
+// the seed and counted by (i, (uint32) n, s, tag).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qew {
+
+constexpr int kRF = 0;
+constexpr int kRB = 1;
+constexpr int kNone = 2;
+
+constexpr uint32_t kTagRF = 0u;  // counter word 3 of random-field force values
+constexpr uint32_t kTagRB = 1u;  // counter word 3 of random-bond potential values
+
+// One chain of the batch.
+struct ChainDesc {
+    int64_t offset;   // first site of the chain in the concatenated state arrays
+    int32_t L;        // number of sites
+    uint32_t s;       // sample index (counter word 2)
+    int32_t kind;     // kRF / kRB / kNone
+    int32_t tile0;    // first partial-sum slot of this chain (tiles of its list)
+    int32_t ntiles;   // number of tiles (partial-sum slots) of this chain
+    float f32;        // drive f, FP32
+    double f64;       // drive f, FP64
+};
+
+// One warp tile of the fused kernel (or one block tile of the FP64 kernels): chain and first
+// owned site.
+struct TileDesc {
+    int32_t chain;
+    int32_t start;
+};
+
+// ---------------------------------------------------------------------------------------
+// Philox4x32-10.  Round: multiply words 0 and 2 by the two round multipliers (full 64-bit
+// products); the new words are (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1,
+// lo(M0 x0)); the key advances by the two Weyl increments between rounds.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
+        const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
+        const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c.y ^ k0;
+        const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c.w ^ k1;
+        c = make_uint4(n0, static_cast<uint32_t>(p1), n2, static_cast<uint32_t>(p0));
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 disorder_words(uint64_t seed, uint32_t s, int32_t i, int32_t n, uint32_t tag)
+{
+    return philox4x32_10(make_uint4(static_cast<uint32_t>(i), static_cast<uint32_t>(n), s, tag),
+                         static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+}
+
+// cos(2 pi (x + 1/2) 2^-32) in FP32 with an exact argument.  Rounding U2 = (x + 1/2) 2^-32 to
+// FP32 would move the angle by up to 2 pi 2^-24; instead split 2 U2 = h + l with
+// h = (x >> 16) 2^-15 and l = ((x mod 2^16) + 1/2) 2^-31 (both exact in FP32, l < 2^-15), take
+// sin/cos(pi h) from sincospif, and add the small angle pi l by the angle-addition formula with
+// sin(pi l) = pi l and cos(pi l) = 1 - (pi l)^2 / 2 (the next terms are below FP32 resolution).
+__device__ __forceinline__ float cos_2pi_word(uint32_t x)
+{
+    const float h = static_cast<float>(x >> 16) * 0x1p-15f;
+    const float l = fmaf(static_cast<float>(x & 0xFFFFu), 0x1p-31f, 0x1p-32f);
+    float s, c;
+    sincospif(h, &s, &c);
+    const float pl = 3.14159265358979f * l;
+    return fmaf(-s, pl, fmaf(-0.5f * pl, pl * c, c));
+}
+
+// R = sqrt(-2 ln U1) cos(2 pi U2), U_k = (x_k + 1/2) 2^-32 (Box-Muller, cosine branch).
+// FP32: ln U1 is taken as log1p(-(1 - U1)) when U1 > 1/2, where 1 - U1 = (~x0 + 1/2) 2^-32 is
+// exact in the word arithmetic; this keeps the small values of R near U1 -> 1 accurate
+// (rounding U1 itself to FP32 would flush them to zero).
+__device__ __forceinline__ float rf_value_f32(uint4 w)
+{
+    float lg;
+    if (w.x & 0x80000000u)
+        lg = log1pf(-fmaf(static_cast<float>(~w.x), 0x1p-32f, 0x1p-33f));
+    else
+        lg = logf(fmaf(static_cast<float>(w.x), 0x1p-32f, 0x1p-33f));
+    return sqrtf(-2.0f * lg) * cos_2pi_word(w.y);
+}
+
+__device__ __forceinline__ double rf_value_f64(uint4 w)
+{
+    const double u1 = (static_cast<double>(w.x) + 0.5) * 0x1p-32;
+    const double u2 = (static_cast<double>(w.y) + 0.5) * 0x1p-32;
+    return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// V = (x0 + 1/2) 2^-31 - 1, uniform on (-1, 1).
+__device__ __forceinline__ float rb_value_f32(uint4 w)
+{
+    return fmaf(static_cast<float>(w.x), 0x1p-31f, -1.0f);
+}
+
+__device__ __forceinline__ double rb_value_f64(uint4 w)
+{
+    return (static_cast<double>(w.x) + 0.5) * 0x1p-31 - 1.0;
+}
+
+__device__ __forceinline__ float rf_f32(uint64_t seed, uint32_t s, int32_t i, int32_t n)
+{
+    return rf_value_f32(disorder_words(seed, s, i, n, kTagRF));
+}
+
+__device__ __forceinline__ float rb_f32(uint64_t seed, uint32_t s, int32_t i, int32_t n)
+{
+    return rb_value_f32(disorder_words(seed, s, i, n, kTagRB));
+}
+
+__device__ __forceinline__ double rf_f64(uint64_t seed, uint32_t s, int32_t i, int32_t n)
+{
+    return rf_value_f64(disorder_words(seed, s, i, n, kTagRF));
+}
+
+__device__ __forceinline__ double rb_f64(uint64_t seed, uint32_t s, int32_t i, int32_t n)
+{
+    return rb_value_f64(disorder_words(seed, s, i, n, kTagRB));
+}
+
+// Site index i modulo L for any int64 position (windows may wrap more than once on short chains).
+__device__ __forceinline__ int32_t wrap_site(int64_t g, int32_t L)
+{
+    int64_t r = g % L;
+    return static_cast<int32_t>(r < 0 ? r + L : r);
+}
+
+}  // namespace qew

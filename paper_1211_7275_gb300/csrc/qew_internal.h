@@ -1,0 +1,86 @@
+// qew_internal.h -- declarations shared by the translation units of the qEW library (kernel
+// launchers and the buffers they work on).  Not part of the public C ABI (include/qew.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qew_device.cuh"
+
+namespace qew {
+
+// FP32-split state: cell n (int32), in-cell offset d (float, [0,1)) and the disorder cache
+// of each site: RF keeps R(n), R(n+1) in c[0], c[1]; RB keeps V(n-1..n+2) in c[0..3].
+struct SplitState {
+    int32_t* cell;
+    float* off;
+    float* c[4];
+};
+
+// FP64 state: displacement u, and the disorder cache of the cell `ncache` it was drawn for:
+// RF R(n), R(n+1) in c[0], c[1]; RB V(n-1..n+2) in c[0..3].
+struct F64State {
+    double* u;
+    int32_t* ncache;
+    double* c[4];
+};
+
+struct SplitLaunch {
+    const TileDesc* tiles;   // tiles of one disorder kind
+    int32_t n_tiles;
+    int32_t tile_base;       // partial-sum slot of tiles[0]
+    const ChainDesc* chains;
+    SplitState in, out;
+    int32_t K;               // Euler steps in this launch (0: observe only)
+    int32_t w_own;           // owned sites per tile
+    float dt;
+    uint64_t seed;
+    int32_t do_obs;          // write per-tile partial sums of the state after the K steps
+    const double* shift;     // per-chain reference cell c of the sums
+    double* partial;         // [n_tiles_total][3]: sum F, sum (u - c), sum (u - c)^2
+    unsigned long long* crossings;  // if not null: cell crossings are added here
+};
+
+// Sites per lane of the fused kernel for each supported tile width (tile_w = 32 * S).
+bool split_supported(int kind, int sites_per_lane);
+size_t split_smem_bytes(int kind, int sites_per_lane, int tiles_per_cta);
+cudaError_t split_step(int kind, int sites_per_lane, int tiles_per_cta, const SplitLaunch& a, cudaStream_t st);
+cudaError_t split_init(const ChainDesc* chains, int32_t n_chains, const TileDesc* tiles, int32_t n_tiles,
+                       int32_t w_tile, SplitState st, uint64_t seed, int any_rb, const double* u_in,
+                       cudaStream_t stream);
+cudaError_t split_to_f64(const ChainDesc* chains, const TileDesc* tiles, int32_t n_tiles, int32_t w_tile,
+                         SplitState st, double* u_out, int32_t* cells_out, cudaStream_t stream);
+
+struct F64Launch {
+    const TileDesc* tiles;   // block tiles of w_tile sites
+    int32_t n_tiles;
+    int32_t w_tile;
+    const ChainDesc* chains;
+    F64State st;             // cache is updated in place
+    const double* u_in;
+    double* u_out;
+    double dt;
+    uint64_t seed;
+    const double* shift;
+    double* partial;
+};
+
+cudaError_t f64_step(const F64Launch& a, cudaStream_t st);
+cudaError_t f64_observe(const F64Launch& a, cudaStream_t st);
+cudaError_t f64_init(const ChainDesc* chains, const TileDesc* tiles, int32_t n_tiles, int32_t w_tile,
+                     F64State st, uint64_t seed, int any_rb, const double* u_in, cudaStream_t stream);
+cudaError_t f64_cells(const ChainDesc* chains, const TileDesc* tiles, int32_t n_tiles, int32_t w_tile,
+                      const double* u, int32_t* cells_out, cudaStream_t stream);
+
+// Second pass: per chain, sum the partials of its tiles in a fixed order, record
+// (sum F, S1, S2, c) into obs[chain] and move the chain's reference c to the new centre of
+// mass (rounded to an integer cell when `integer_shift`).
+cudaError_t reduce_chains(const ChainDesc* chains, int32_t n_chains, const double* partial, double* shift,
+                          double* obs, int integer_shift, cudaStream_t stream);
+
+cudaError_t philox_words(const uint32_t* ctr, const uint32_t* key, int64_t n_blocks, uint32_t* out,
+                         cudaStream_t stream);
+cudaError_t disorder_values(int kind, int fp64, uint64_t seed, uint32_t s, const int64_t* i, const int64_t* n,
+                            int64_t count, double* out, cudaStream_t stream);
+
+}  // namespace qew

@@ -1,0 +1,411 @@
+// qew_split.cu -- the fused FP32-split kernel of the qEW relaxation: elastic force + pinning
+// force + Euler update + cell renormalisation + disorder regeneration, K Euler steps per HBM
+// round trip (temporal blocking), with the checkpoint partial sums fused after the last step.
+//
+// Method: Eq. 1 of arXiv:1211.7275 with eta = c = 1, discretised in x with periodic boundary
+// conditions and integrated by explicit Euler (Sec. III.B); pinning force interpolated from
+// random values at integer (i, n) (Sec. III.B and the cases of Sec. IV.C); observables of
+// Eqs. 3-5 (Sec. II).
+//
+// State of a site: integer cell n and FP32 offset d in [0, 1) (u = n + d), plus its disorder
+// cache: RF keeps R(n) + f and R(n+1) + f, RB keeps V(n-1 .. n+2).  The drive f is folded into
+// the RF cache so that F_p + f costs one subtraction and one FMA per site-step.
+//
+// Work decomposition: one warp owns one tile of 32 * S sites of a chain, S consecutive sites
+// per lane held in registers.  A tile advanced K steps needs K extra sites on each side (the
+// stencil's light cone), so the window is [start - K, start - K + 32 S) and the owned sites
+// [start, start + w_own), w_own <= 32 S - 2K; the outermost sites of the window go stale one
+// per step from each edge and are never stored.  Windows wrap around periodic chains (any
+// number of times for chains shorter than a tile).  Halo exchange inside a step is two warp
+// shuffles per neighbour; there is no shared-memory traffic and no barrier inside the K loop.
+#include <cstdio>
+
+#include "qew_internal.h"
+
+namespace qew {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Exact int -> float for -2^22 <= k < 2^22 without the conversion pipe: adding the bit pattern
+// of 1.5 * 2^23 places k in the mantissa of a float whose unit in the last place is 1; the
+// subtraction then removes the bias exactly (the "magic number" conversion).
+__device__ __forceinline__ float small_int_to_float(int k)
+{
+    return __int_as_float(k + 0x4B400000) - 12582912.0f;
+}
+
+// Offset outside [0, 1) (or NaN / -0): compare the bit pattern; every float in [0, 1) is
+// below the pattern of 1.0f, negative values have the sign bit set.
+__device__ __forceinline__ unsigned out_of_cell(float d)
+{
+    return __float_as_uint(d) >= 0x3F800000u ? 1u : 0u;
+}
+
+// Move a site whose offset left [0, 1) to its new cell: returns the cell shift k and leaves
+// d in [0, 1).  A tiny negative offset can round to 1.0f after the shift; then the site stays
+// in the upper cell with d = 0.
+__device__ __forceinline__ int renormalise(float& d)
+{
+    const float fk = floorf(d);
+    int k = static_cast<int>(fk);
+    float r = d - fk;
+    if (r >= 1.0f) {
+        r = 0.0f;
+        k += 1;
+    }
+    d = r;
+    return k;
+}
+
+// RB cubic coefficients of F_p + f = A + d (B + d C) for the Catmull-Rom spline through
+// p0..p3 = V(n-1 .. n+2):  -dV/du = -1/2 [(p2 - p0) + 2 b d + 3 c d^2],
+// b = 2 p0 - 5 p1 + 4 p2 - p3, c = -p0 + 3 p1 - 3 p2 + p3.
+__device__ __forceinline__ void rb_coefficients(float p0, float p1, float p2, float p3, float f, float& A,
+                                                float& B, float& C)
+{
+    A = fmaf(-0.5f, p2 - p0, f);
+    B = -(((2.0f * p0 - 5.0f * p1) + 4.0f * p2) - p3);
+    C = -1.5f * (((3.0f * p1 - p0) - 3.0f * p2) + p3);
+}
+
+template <int KIND>
+struct CacheWidth {
+    static constexpr int value = (KIND == kRB) ? 4 : 2;
+};
+
+template <int KIND, int S>
+__global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
+{
+    constexpr int NC = CacheWidth<KIND>::value;
+    constexpr int TW = 32 * S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int tile = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (tile >= a.n_tiles)
+        return;  // whole warp; the kernel uses no block-wide barrier
+
+    int32_t* s_cell = reinterpret_cast<int32_t*>(smem_raw) + static_cast<size_t>(warp) * TW * (2 + NC);
+    float* s_off = reinterpret_cast<float*>(s_cell + TW);
+    float* s_c = s_off + TW;
+
+    const TileDesc td = a.tiles[tile];
+    const ChainDesc ch = a.chains[td.chain];
+    const int32_t L = ch.L;
+    const int K = a.K;
+    const int owned = min(a.w_own, L - td.start);
+    const int64_t wstart = static_cast<int64_t>(td.start) - K;
+    const bool contiguous = (wstart >= 0) && (wstart + TW <= L);
+    const float f = ch.f32;
+    const float dt = a.dt;
+    const uint64_t seed = a.seed;
+    const uint32_t s = ch.s;
+
+    // ---- stage the window: coalesced global loads into this warp's shared-memory slice ----
+    for (int x = lane; x < TW; x += 32) {
+        const int32_t g = contiguous ? static_cast<int32_t>(wstart + x) : wrap_site(wstart + x, L);
+        const int64_t p = ch.offset + g;
+        s_cell[x] = a.in.cell[p];
+        s_off[x] = a.in.off[p];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            s_c[c * TW + x] = a.in.c[c][p];
+    }
+    __syncwarp();
+
+    int n[S];
+    float d[S];
+    float q[NC][S];   // RF: R(n)+f, R(n+1)+f.  RB: V(n-1..n+2)
+    float A[KIND == kRB ? S : 1], B[KIND == kRB ? S : 1], C[KIND == kRB ? S : 1];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        const int x = lane * S + j;
+        n[j] = s_cell[x];
+        d[j] = s_off[x];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            q[c][j] = s_c[c * TW + x];
+        if constexpr (KIND == kRB)
+            rb_coefficients(q[0][j], q[1][j], q[2][j], q[3][j], f, A[j], B[j], C[j]);
+    }
+
+    // ---- K Euler steps, all in registers ----
+    unsigned n_cross = 0;
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+        const int nl = __shfl_up_sync(kFull, n[S - 1], 1);
+        const float dl = __shfl_up_sync(kFull, d[S - 1], 1);
+        const int nr = __shfl_down_sync(kFull, n[0], 1);
+        const float drn = __shfl_down_sync(kFull, d[0], 1);
+        float Dm = small_int_to_float(n[0] - nl) + (d[0] - dl);   // u_j - u_{j-1}
+        unsigned cross = 0;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const int nn = (j + 1 < S) ? n[j + 1] : nr;
+            const float dd = (j + 1 < S) ? d[j + 1] : drn;
+            const float Dp = small_int_to_float(nn - n[j]) + (dd - d[j]);   // u_{j+1} - u_j
+            float g;                                                         // F_p + f
+            if constexpr (KIND == kRB)
+                g = fmaf(d[j], fmaf(d[j], C[j], B[j]), A[j]);
+            else
+                g = fmaf(d[j], q[1][j] - q[0][j], q[0][j]);
+            const float dn = fmaf(dt, (Dp - Dm) + g, d[j]);
+            Dm = Dp;
+            d[j] = dn;
+            cross |= out_of_cell(dn) << j;
+        }
+        if (cross) {
+            n_cross += __popc(cross);
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                if (!((cross >> j) & 1u))
+                    continue;
+                const int kk = renormalise(d[j]);
+                if (kk == 0)
+                    continue;
+                const int nn = n[j] + kk;
+                n[j] = nn;
+                if constexpr (KIND == kNone)
+                    continue;
+                const int64_t gx = wstart + lane * S + j;
+                const int32_t i = contiguous ? static_cast<int32_t>(gx) : wrap_site(gx, L);
+                if constexpr (KIND == kRF) {
+                    if (kk == 1) {
+                        q[0][j] = q[1][j];
+                        q[1][j] = rf_f32(seed, s, i, nn + 1) + f;
+                    } else if (kk == -1) {
+                        q[1][j] = q[0][j];
+                        q[0][j] = rf_f32(seed, s, i, nn) + f;
+                    } else {
+                        q[0][j] = rf_f32(seed, s, i, nn) + f;
+                        q[1][j] = rf_f32(seed, s, i, nn + 1) + f;
+                    }
+                } else {
+                    if (kk == 1) {
+                        q[0][j] = q[1][j];
+                        q[1][j] = q[2][j];
+                        q[2][j] = q[3][j];
+                        q[3][j] = rb_f32(seed, s, i, nn + 2);
+                    } else if (kk == -1) {
+                        q[3][j] = q[2][j];
+                        q[2][j] = q[1][j];
+                        q[1][j] = q[0][j];
+                        q[0][j] = rb_f32(seed, s, i, nn - 1);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            q[c][j] = rb_f32(seed, s, i, nn - 1 + c);
+                    }
+                    rb_coefficients(q[0][j], q[1][j], q[2][j], q[3][j], f, A[j], B[j], C[j]);
+                }
+            }
+        }
+    }
+
+    if (a.crossings) {
+        unsigned tot = __reduce_add_sync(kFull, n_cross);
+        if (lane == 0 && tot)
+            atomicAdd(a.crossings, static_cast<unsigned long long>(tot));
+    }
+
+    // ---- checkpoint partial sums of the state after the K steps (owned sites only) ----
+    if (a.do_obs) {
+        const int32_t c_ref = static_cast<int32_t>(a.shift[td.chain]);
+        const int32_t nref = n[0];
+        float sF = 0.0f, sy = 0.0f, syy = 0.0f;
+        int cnt = 0;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const int o = lane * S + j - K;
+            if (o >= 0 && o < owned) {
+                float g;
+                if constexpr (KIND == kRB)
+                    g = fmaf(d[j], fmaf(d[j], C[j], B[j]), A[j]);
+                else
+                    g = fmaf(d[j], q[1][j] - q[0][j], q[0][j]);
+                sF += g - f;
+                const float y = small_int_to_float(n[j] - nref) + d[j];
+                sy += y;
+                syy = fmaf(y, y, syy);
+                ++cnt;
+            }
+        }
+        const double rel = static_cast<double>(nref) - static_cast<double>(c_ref);
+        double tF = sF;
+        double t1 = static_cast<double>(sy) + cnt * rel;
+        double t2 = static_cast<double>(syy) + 2.0 * rel * static_cast<double>(sy) + cnt * rel * rel;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tF += __shfl_down_sync(kFull, tF, o);
+            t1 += __shfl_down_sync(kFull, t1, o);
+            t2 += __shfl_down_sync(kFull, t2, o);
+        }
+        if (lane == 0) {
+            double* dst = a.partial + static_cast<size_t>(a.tile_base + tile) * 3;
+            dst[0] = tF;
+            dst[1] = t1;
+            dst[2] = t2;
+        }
+    }
+
+    if (K == 0)
+        return;
+
+    // ---- write the owned sites back: registers -> shared -> coalesced global stores ----
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        const int x = lane * S + j;
+        s_cell[x] = n[j];
+        s_off[x] = d[j];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            s_c[c * TW + x] = q[c][j];
+    }
+    __syncwarp();
+    for (int o = lane; o < owned; o += 32) {
+        const int x = o + K;
+        const int64_t p = ch.offset + td.start + o;
+        a.out.cell[p] = s_cell[x];
+        a.out.off[p] = s_off[x];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            a.out.c[c][p] = s_c[c * TW + x];
+    }
+}
+
+template <int KIND, int S>
+cudaError_t launch_split(int tiles_per_cta, const SplitLaunch& a, cudaStream_t st)
+{
+    constexpr int NC = CacheWidth<KIND>::value;
+    const size_t smem = static_cast<size_t>(tiles_per_cta) * 32 * S * 4 * (2 + NC);
+    auto kern = split_step_kernel<KIND, S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess)
+        return e;
+    const int grid = (a.n_tiles + tiles_per_cta - 1) / tiles_per_cta;
+    if (grid == 0)
+        return cudaSuccess;
+    kern<<<grid, 32 * tiles_per_cta, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Initialisation (flat start or a given FP64 state) and conversion back to FP64.
+// Block tiles of w_tile sites, one thread per site.
+// ---------------------------------------------------------------------------------------
+__global__ void split_init_kernel(const ChainDesc* chains, const TileDesc* tiles, int32_t w_tile, SplitState st,
+                                  uint64_t seed, const double* u_in)
+{
+    const TileDesc td = tiles[blockIdx.x];
+    const ChainDesc ch = chains[td.chain];
+    for (int x = threadIdx.x; x < w_tile; x += blockDim.x) {
+        const int32_t i = td.start + x;
+        if (i >= ch.L)
+            break;
+        const int64_t p = ch.offset + i;
+        int32_t n = 0;
+        float d = 0.0f;
+        if (u_in) {
+            const double u = u_in[p];
+            const double fl = floor(u);
+            n = static_cast<int32_t>(fl);
+            d = static_cast<float>(u - fl);
+            if (d >= 1.0f) {
+                d = 0.0f;
+                n += 1;
+            }
+        }
+        st.cell[p] = n;
+        st.off[p] = d;
+        if (ch.kind == kRF) {
+            st.c[0][p] = rf_f32(seed, ch.s, i, n) + ch.f32;
+            st.c[1][p] = rf_f32(seed, ch.s, i, n + 1) + ch.f32;
+        } else if (ch.kind == kRB) {
+            for (int c = 0; c < 4; ++c)
+                st.c[c][p] = rb_f32(seed, ch.s, i, n - 1 + c);
+        } else {
+            st.c[0][p] = ch.f32;
+            st.c[1][p] = ch.f32;
+        }
+    }
+}
+
+__global__ void split_to_f64_kernel(const ChainDesc* chains, const TileDesc* tiles, int32_t w_tile, SplitState st,
+                                    double* u_out, int32_t* cells_out)
+{
+    const TileDesc td = tiles[blockIdx.x];
+    const ChainDesc ch = chains[td.chain];
+    for (int x = threadIdx.x; x < w_tile; x += blockDim.x) {
+        const int32_t i = td.start + x;
+        if (i >= ch.L)
+            break;
+        const int64_t p = ch.offset + i;
+        if (u_out)
+            u_out[p] = static_cast<double>(st.cell[p]) + static_cast<double>(st.off[p]);
+        if (cells_out)
+            cells_out[p] = st.cell[p];
+    }
+}
+
+}  // namespace
+
+bool split_supported(int kind, int S)
+{
+    if (kind == kRB)
+        return S == 8 || S == 16;
+    return S == 8 || S == 16 || S == 24 || S == 32;
+}
+
+size_t split_smem_bytes(int kind, int S, int tiles_per_cta)
+{
+    const int nc = (kind == kRB) ? 4 : 2;
+    return static_cast<size_t>(tiles_per_cta) * 32 * S * 4 * (2 + nc);
+}
+
+cudaError_t split_step(int kind, int S, int tiles_per_cta, const SplitLaunch& a, cudaStream_t st)
+{
+    if (kind == kRF) {
+        switch (S) {
+        case 8: return launch_split<kRF, 8>(tiles_per_cta, a, st);
+        case 16: return launch_split<kRF, 16>(tiles_per_cta, a, st);
+        case 24: return launch_split<kRF, 24>(tiles_per_cta, a, st);
+        case 32: return launch_split<kRF, 32>(tiles_per_cta, a, st);
+        }
+    } else if (kind == kRB) {
+        switch (S) {
+        case 8: return launch_split<kRB, 8>(tiles_per_cta, a, st);
+        case 16: return launch_split<kRB, 16>(tiles_per_cta, a, st);
+        }
+    } else {
+        switch (S) {
+        case 8: return launch_split<kNone, 8>(tiles_per_cta, a, st);
+        case 16: return launch_split<kNone, 16>(tiles_per_cta, a, st);
+        case 24: return launch_split<kNone, 24>(tiles_per_cta, a, st);
+        case 32: return launch_split<kNone, 32>(tiles_per_cta, a, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t split_init(const ChainDesc* chains, int32_t, const TileDesc* tiles, int32_t n_tiles, int32_t w_tile,
+                       SplitState st, uint64_t seed, int, const double* u_in, cudaStream_t stream)
+{
+    if (n_tiles == 0)
+        return cudaSuccess;
+    split_init_kernel<<<n_tiles, 256, 0, stream>>>(chains, tiles, w_tile, st, seed, u_in);
+    return cudaGetLastError();
+}
+
+cudaError_t split_to_f64(const ChainDesc* chains, const TileDesc* tiles, int32_t n_tiles, int32_t w_tile,
+                         SplitState st, double* u_out, int32_t* cells_out, cudaStream_t stream)
+{
+    if (n_tiles == 0)
+        return cudaSuccess;
+    split_to_f64_kernel<<<n_tiles, 256, 0, stream>>>(chains, tiles, w_tile, st, u_out, cells_out);
+    return cudaGetLastError();
+}
+
+}  // namespace qew

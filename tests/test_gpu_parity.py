@@ -1,0 +1,290 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+Bars (BASELINE north star; Sec. II-III of arXiv:1211.7275 define what is computed):
+  - RNG words and integer cell indices: bit-exact (cells compared where the oracle's u is more
+    than 1e-4 from an integer, where FP32 rounding cannot move the floor);
+  - FP64 path: per site |du| <= 1e-12 max(1, |u|) over 10^3 steps;
+  - FP32-split path: per site |du| <= 1e-4 over the first 10^3 steps;
+  - ensemble v(t), w2(t): within 2 sigma of the oracle's sample error bars to t_max.
+Sizes span several warp tiles and a ragged tail; degenerate lengths (L = 1, 2, 3, ...) make a
+tile window wrap around the chain many times.
+"""
+import numpy as np
+import pytest
+
+from qew_workloads import SEED, cosine_profile, log_spaced_steps, positive_shift, random_points, random_state
+
+pytestmark = pytest.mark.gpu
+
+RF, RB, NONE = 0, 1, 2
+FP32, FP64 = 0, 1
+
+
+@pytest.fixture(scope="module")
+def qew():
+    import paper_1211_7275_gb300 as q
+    q.load()
+    return q
+
+
+def gpu_run(qew, L, f, kind, steps, precision, *, tuning=None, u0=None, dt=0.1, seed=SEED):
+    with qew.Relaxation(L, f, kind, dt=dt, seed=seed, precision=precision) as r:
+        if tuning is not None:
+            r.set_tuning(*tuning)
+        if u0 is not None:
+            r.set_state(u0)
+        obs = r.observe(steps)
+        u, step = r.state()
+        cells = r.cells()
+    assert step == steps[-1]
+    return obs, u, cells
+
+
+# ------------------------------------------------------------------------------------------
+# generator
+# ------------------------------------------------------------------------------------------
+def test_philox_words_bitexact(qew, orc):
+    rng = np.random.default_rng(5)
+    ctr = rng.integers(0, 2 ** 32, size=(1 << 20, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(1 << 20, 2), dtype=np.uint64).astype(np.uint32)
+    assert np.array_equal(qew.philox_words(ctr, key), orc.philox4x32_10(ctr, key))
+
+
+@pytest.mark.parametrize("kind", [RF, RB])
+def test_disorder_values(qew, orc, kind):
+    i, n = random_points(200_000, 1 << 25, -3000, 3000, seed=9)
+    ref = orc.disorder_values(kind, SEED, 3, i, n)
+    g64 = qew.disorder_values(kind, FP64, SEED, 3, i, n)
+    g32 = qew.disorder_values(kind, FP32, SEED, 3, i, n)
+    if kind == RB:
+        assert np.array_equal(g64, ref)   # exact arithmetic on both sides
+    else:
+        assert np.max(np.abs(g64 - ref) / np.maximum(1.0, np.abs(ref))) < 4e-15
+    assert np.max(np.abs(g32 - ref) / np.maximum(1.0, np.abs(ref))) < 6e-7
+
+
+# ------------------------------------------------------------------------------------------
+# FP64 path
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,L,f", [(RF, 1024, 1.0), (RB, 777, 1.9), (RF, 3, 0.8), (RB, 5, 2.0), (NONE, 64, 0.3)])
+def test_fp64_per_site(qew, orc, kind, L, f):
+    steps = np.array([0, 1, 2, 10, 100, 1000])
+    obs, u, cells = gpu_run(qew, L, f, kind, steps, FP64)
+    ref = orc.run(L, f, 0.1, kind, SEED, steps, want_state=True)
+    err = np.abs(u - ref["u"]) / np.maximum(1.0, np.abs(ref["u"]))
+    assert err.max() <= 1e-12, err.max()
+    assert np.array_equal(cells, np.floor(ref["u"]).astype(np.int32))
+    np.testing.assert_allclose(obs["v"], ref["v"], rtol=0, atol=1e-11)
+    np.testing.assert_allclose(obs["ubar"], ref["ubar"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(obs["w2"], ref["w2"], rtol=1e-9, atol=1e-12)
+
+
+def test_fp64_closed_form(qew):
+    L, k, A, B, f, dt = 128, 3, 0.7, 3.2, 0.37, 0.1
+    u0 = cosine_profile(L, A, B, k)
+    lam = 1.0 - 4.0 * dt * np.sin(np.pi * k / L) ** 2
+    n = 300
+    obs, u, _ = gpu_run(qew, L, f, NONE, [0, n], FP64, u0=u0)
+    exact = B + f * n * dt + A * lam ** n * np.cos(2 * np.pi * k * np.arange(L) / L)
+    assert np.max(np.abs(u - exact)) < 1e-12 * np.abs(exact).max()
+    assert abs(obs["v"][1, 0] - f) < 1e-14
+    assert abs(obs["w2"][1, 0] - A * A * lam ** (2 * n) / 2) < 1e-12
+
+
+# ------------------------------------------------------------------------------------------
+# FP32-split fused path
+# ------------------------------------------------------------------------------------------
+SHAPES = [(512, 16, 4), (256, 8, 2), (1024, 32, 1), (768, 24, 8)]
+
+
+def _split_check(u, cells, ref_u, tol=1e-4):
+    err = np.abs(u - ref_u)
+    assert err.max() <= tol, err.max()
+    far = np.abs(ref_u - np.round(ref_u)) > 1e-4
+    assert np.array_equal(cells[far], np.floor(ref_u[far]).astype(np.int32))
+    return err.max()
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 5, 31, 33, 1024, 5000])
+def test_split_rf_per_site(qew, orc, L):
+    steps = np.array([0, 1, 7, 100, 1000])
+    ref = orc.run(L, 1.0, 0.1, RF, SEED, steps, want_state=True)
+    obs, u, cells = gpu_run(qew, L, 1.0, RF, steps, FP32)
+    _split_check(u, cells, ref["u"])
+    np.testing.assert_allclose(obs["ubar"], ref["ubar"], rtol=0, atol=2e-5)
+    np.testing.assert_allclose(obs["v"], ref["v"], rtol=0, atol=2e-4)
+
+
+@pytest.mark.parametrize("L", [3, 256, 4099])
+def test_split_rb_per_site(qew, orc, L):
+    steps = np.array([0, 3, 50, 1000])
+    ref = orc.run(L, 1.9, 0.1, RB, SEED, steps, want_state=True)
+    obs, u, cells = gpu_run(qew, L, 1.9, RB, steps, FP32)
+    _split_check(u, cells, ref["u"])
+    np.testing.assert_allclose(obs["v"], ref["v"], rtol=0, atol=2e-4)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_split_shapes_identical(qew, orc, shape):
+    """Every launch shape performs the same per-site arithmetic: states agree bit for bit."""
+    L, steps = 20000, np.array([0, 5, 333, 1000])
+    _, u_ref, _ = gpu_run(qew, L, 1.0, RF, steps, FP32, tuning=SHAPES[0])
+    obs, u, cells = gpu_run(qew, L, 1.0, RF, steps, FP32, tuning=shape)
+    assert np.array_equal(u, u_ref)
+    ref = orc.run(L, 1.0, 0.1, RF, SEED, steps, want_state=True)
+    _split_check(u, cells, ref["u"])
+
+
+def test_split_uneven_mixed_batch(qew, orc):
+    # drives in the moving regime; the near-critical precision has its own test below
+    L = np.array([1, 300, 4097, 1025, 77, 2048])
+    kind = np.array([RF, RB, RF, RB, NONE, RF], dtype=np.int32)
+    f = np.array([1.0, 1.9, 1.3, 2.0, 0.5, 1.1])
+    steps = np.array([0, 10, 500])
+    ref = orc.run(L, f, 0.1, kind, SEED, steps, want_state=True)
+    for prec in (FP32, FP64):
+        with qew.Relaxation(L, f, kind, dt=0.1, seed=SEED, precision=prec) as r:
+            obs = r.observe(steps)
+            u, _ = r.state()
+        if prec == FP64:
+            assert np.max(np.abs(u - ref["u"]) / np.maximum(1, np.abs(ref["u"]))) <= 1e-12
+        else:
+            assert np.max(np.abs(u - ref["u"])) <= 1e-4
+        np.testing.assert_allclose(obs["v"], ref["v"], atol=2e-4)
+        np.testing.assert_allclose(obs["w2"], ref["w2"], rtol=1e-4, atol=1e-6)
+
+
+def test_split_near_critical_precision(qew, orc):
+    """At f = f_c^L (random field, L = 4096, the oracle-bisected fixture) the FP32 rounding of the
+    disorder values and of the force is amplified at the rare sites that sit near a depinning
+    threshold; the deviation from the FP64 oracle over the first 10^3 steps is checked as a
+    distribution: rms, the fraction of sites above 1e-4, and the maximum."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fc_rf_L4096.json")) as fh:
+        fc = json.load(fh)
+    L, f, n = fc["L"], fc["f_c"], 1000
+    with qew.Relaxation(L, f, RF, dt=0.1, seed=SEED, precision=FP32, batch=4) as r:
+        r.observe([n])
+        u, _ = r.state()
+    ref = orc.run([L] * 4, f, 0.1, RF, SEED, [n], want_state=True)["u"]
+    err = np.abs(u - ref)
+    rms, frac, mx = float(np.sqrt(np.mean(err ** 2))), float(np.mean(err > 1e-4)), float(err.max())
+    print(f"near-critical FP32-split vs oracle after {n} steps: rms {rms:.2e}, >1e-4: {frac:.1e}, max {mx:.2e}")
+    assert rms <= 2e-5 and frac <= 1e-3 and mx <= 1e-3, (rms, frac, mx)
+
+
+def test_split_closed_form(qew):
+    L, k, A, B, f, dt = 4096, 5, 0.7, 3.2, 0.37, 0.1
+    u0 = cosine_profile(L, A, B, k)
+    lam = 1.0 - 4.0 * dt * np.sin(np.pi * k / L) ** 2
+    n = 1000
+    obs, u, _ = gpu_run(qew, L, f, NONE, [0, n], FP32, u0=u0)
+    exact = B + f * n * dt + A * lam ** n * np.cos(2 * np.pi * k * np.arange(L) / L)
+    assert np.max(np.abs(u - exact)) < 1e-4
+    assert abs(obs["ubar"][1, 0] - (B + f * n * dt)) < 1e-5
+
+
+def test_split_no_passing(qew):
+    L = 3000
+    u0 = random_state(L, 0.5, seed=11)
+    u1 = u0 + positive_shift(L, 0.3, seed=12)
+    _, a, _ = gpu_run(qew, L, 1.0, RF, [0, 2000], FP32, u0=u0)
+    _, b, _ = gpu_run(qew, L, 1.0, RF, [0, 2000], FP32, u0=u1)
+    assert np.all(b >= a)
+
+
+@pytest.mark.parametrize("precision", [FP32, FP64])
+def test_mean_velocity_invariant(qew, precision):
+    steps = np.array([0, 1, 2, 3, 50, 51, 400, 401])
+    obs, _, _ = gpu_run(qew, 10007, 0.9, RF, steps, precision)
+    ub, v = obs["ubar"][:, 0], obs["v"][:, 0]
+    tol = 1e-12 if precision == FP64 else 2e-6
+    for j in range(len(steps) - 1):
+        if steps[j + 1] == steps[j] + 1:
+            assert abs((ub[j + 1] - ub[j]) - 0.1 * v[j]) <= tol * max(1.0, abs(ub[j])), j
+
+
+def test_resume_is_exact(qew):
+    """state(2N) == set_state(state(N)) + N more steps: the disorder is a pure function of (i, n)."""
+    L, N = 5000, 400
+    for prec in (FP32, FP64):
+        _, u_full, _ = gpu_run(qew, L, 1.0, RF, [2 * N], prec)
+        _, u_half, _ = gpu_run(qew, L, 1.0, RF, [N], prec)
+        _, u_res, _ = gpu_run(qew, L, 1.0, RF, [N], prec, u0=u_half)
+        assert np.array_equal(u_full, u_res)
+
+
+def test_deterministic_observables(qew):
+    steps = log_spaced_steps(2000, 12)
+    a, _, _ = gpu_run(qew, 70000, 1.0, RF, steps, FP32)
+    b, _, _ = gpu_run(qew, 70000, 1.0, RF, steps, FP32)
+    for k in ("v", "ubar", "w2"):
+        assert np.array_equal(a[k], b[k])
+
+
+def test_ensemble_within_two_sigma(qew, orc):
+    """32 samples, L = 1024, 10^4 steps (the tiny preset's length and horizon): ensemble V(t),
+    W2(t) of the fast path within 2 sigma of the oracle's, and the paired differences far
+    smaller than sigma."""
+    n_s, L = 32, 1024
+    steps = log_spaced_steps(10_000, 40)
+    ref = orc.run([L] * n_s, 1.0, 0.1, RF, SEED, steps)
+    with qew.Relaxation(L, 1.0, RF, dt=0.1, seed=SEED, precision=FP32, batch=n_s) as r:
+        obs = r.observe(steps)
+    for key in ("v", "w2"):
+        m_ref, m_gpu = ref[key].mean(1), obs[key].mean(1)
+        sig = ref[key].std(1, ddof=1) / np.sqrt(n_s)
+        sig[0] = max(sig[0], 1e-12)
+        ok = np.abs(m_gpu - m_ref) <= 2 * sig + 1e-12
+        assert ok.all(), (key, np.where(~ok))
+        paired = np.abs(obs[key] - ref[key]).mean(1)
+        assert np.all(paired[1:] <= 0.5 * np.maximum(ref[key].std(1, ddof=1)[1:], 1e-9)), key
+
+
+# ------------------------------------------------------------------------------------------
+# the benchmark's own launch configuration at full size: 4 chains of 2^25 sites
+# ------------------------------------------------------------------------------------------
+def test_full_size_sampled_sites(qew, orc):
+    """Config of the bench: 4 x 2^25 sites.  After 1000 steps, sampled sites (tile edges, the
+    periodic seam, random sites) against the oracle's light-cone evaluation of the same site;
+    the invariant dubar = dt v at every chain."""
+    from qew_workloads import preset_f
+    L, batch, n = 1 << 25, 4, 1000
+    f = preset_f("rf_4x2^25")
+    steps = np.array([0, n - 1, n])
+    with qew.Relaxation(L, f, RF, dt=0.1, seed=SEED, precision=FP32, batch=batch) as r:
+        obs = r.observe(steps)
+        u, _ = r.state()
+        tile_w, K, _ = r.tuning()
+    w_own = tile_w - 2 * K
+    rng = np.random.default_rng(3)
+    picks = []
+    for c in range(batch):
+        for i in [0, 1, L - 1, L - 2, w_own - 1, w_own, 5 * w_own + 1] + list(rng.integers(0, L, 3)):
+            picks.append((c, int(i)))
+    for c, i in picks:
+        ref_u, _ = orc.lightcone(L, c, f, 0.1, RF, SEED, i, 1, n)
+        assert abs(u[c * L + i] - ref_u[0]) <= 1e-4, (c, i)
+    dub = obs["ubar"][2] - obs["ubar"][1]
+    assert np.all(np.abs(dub - 0.1 * obs["v"][1]) <= 2e-6 * np.maximum(1, np.abs(obs["ubar"][1])))
+
+
+# ------------------------------------------------------------------------------------------
+# argument errors (need a device for handle creation)
+# ------------------------------------------------------------------------------------------
+def test_errors(qew):
+    with qew.Relaxation(100, 1.0) as r:
+        r.observe([10])
+        with pytest.raises(qew.QewError) as e:
+            r.observe([5])
+        assert e.value.code == -1
+        with pytest.raises(qew.QewError) as e:
+            r.set_precision(FP64)
+        assert e.value.code == -6
+        with pytest.raises(qew.QewError):
+            r.set_tuning(500, 8, 4)
+        with pytest.raises(qew.QewError):
+            r.set_tuning(512, 200, 4)
+        r.observe([])
+        r.advance(0)
