@@ -48,7 +48,7 @@ enum qew_status {
     QEW_EINVAL = -1,     /* invalid argument (message says which) */
     QEW_ENOMEM = -2,     /* device or host allocation failed */
     QEW_ECUDA = -3,      /* a CUDA call failed (message carries cudaGetErrorString) */
-    QEW_ETIMEOUT = -4,   /* reserved: a bounded device wait gave up */
+    QEW_ETIMEOUT = -4,   /* a bounded device wait (bulk-copy completion) gave up */
     QEW_ENONFINITE = -5, /* an observable came out NaN or infinite */
     QEW_ESTATE = -6      /* call not allowed in the handle's current state */
 };

@@ -116,6 +116,7 @@ struct qew_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     unsigned long long* d_crossings = nullptr;
+    int32_t* d_error = nullptr;   // set by a kernel whose bounded wait gave up
 
     std::string err;
 };
@@ -193,6 +194,7 @@ void free_all(qew_ctx* h)
 {
     free_events(h);
     dev_free(h->d_crossings);
+    dev_free(h->d_error);
     free_split(h);
     free_f64(h);
     dev_free(h->d_chains);
@@ -350,6 +352,7 @@ SplitLaunch split_args(qew_ctx* h, int kind, int K, int do_obs, SplitState in, S
     a.shift = h->d_shift;
     a.partial = h->d_partial;
     a.crossings = h->stats_on ? h->d_crossings : nullptr;
+    a.error = h->d_error;
     return a;
 }
 
@@ -598,6 +601,10 @@ int create_impl(qew_handle* out, int32_t n_chains, const int64_t* L, const doubl
             rc = alloc_state(h);
         if (rc == QEW_OK) {
             cudaError_t e = dev_alloc(&h->d_shift, static_cast<size_t>(n_chains));
+            if (e == cudaSuccess)
+                e = dev_alloc(&h->d_error, 1);
+            if (e == cudaSuccess)
+                e = cudaMemset(h->d_error, 0, sizeof(int32_t));
             if (e != cudaSuccess)
                 rc = cuda_fail(h, e, "allocating reference shifts");
         }
@@ -620,6 +627,18 @@ int check_handle(qew_handle h)
 {
     if (!h)
         return fail(nullptr, QEW_EINVAL, "handle must not be NULL");
+    return QEW_OK;
+}
+
+// A kernel whose bounded wait on a bulk copy gave up leaves 1 in d_error; report it once.
+int check_device_error(qew_ctx* h)
+{
+    int32_t flag = 0;
+    QEW_CUDA(h, cudaMemcpy(&flag, h->d_error, sizeof(flag), cudaMemcpyDeviceToHost), "reading the error flag");
+    if (flag) {
+        cudaMemset(h->d_error, 0, sizeof(int32_t));
+        return fail(h, QEW_ETIMEOUT, "a bounded wait for a bulk copy gave up; the state is no longer valid");
+    }
     return QEW_OK;
 }
 
@@ -668,6 +687,8 @@ int observe_impl(qew_ctx* h, const int64_t* steps, int32_t n_times, double* v_ou
     QEW_CUDA(h, cudaMemcpyAsync(h->h_obs, h->d_obs, per * n_times * sizeof(double), cudaMemcpyDeviceToHost,
                                 h->stream), "copying observables to the host");
     QEW_CUDA(h, cudaStreamSynchronize(h->stream), "running the relaxation");
+    if (int rc2 = check_device_error(h))
+        return rc2;
     bool finite = true;
     for (int32_t k = 0; k < n_times; ++k) {
         for (int32_t c = 0; c < h->n_chains; ++c) {
@@ -725,6 +746,8 @@ int get_state_impl(qew_ctx* h, double* u_out, int32_t* cells_out, int64_t* step_
         e = cudaStreamSynchronize(h->stream);
     if (rc == QEW_OK && e != cudaSuccess)
         rc = cuda_fail(h, e, "reading the state");
+    if (rc == QEW_OK)
+        rc = check_device_error(h);
     dev_free(d_u);
     dev_free(d_c);
     return rc;

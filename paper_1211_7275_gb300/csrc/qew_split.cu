@@ -21,6 +21,7 @@
 #include <cstdio>
 
 #include "qew_internal.h"
+#include "qew_tma.cuh"
 
 namespace qew {
 namespace {
@@ -69,6 +70,13 @@ __device__ __forceinline__ void rb_coefficients(float p0, float p1, float p2, fl
     C = -1.5f * (((3.0f * p1 - p0) - 3.0f * p2) + p3);
 }
 
+// Chain-local index of window position x (window start wstart).
+__device__ __forceinline__ int32_t site_index(int64_t wstart, int x, bool contiguous, int32_t L)
+{
+    const int64_t g = wstart + x;
+    return contiguous ? static_cast<int32_t>(g) : wrap_site(g, L);
+}
+
 template <int KIND>
 struct CacheWidth {
     static constexpr int value = (KIND == kRB) ? 4 : 2;
@@ -79,7 +87,8 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
 {
     constexpr int NC = CacheWidth<KIND>::value;
     constexpr int TW = 32 * S;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t s_bar[8];
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -103,17 +112,50 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
     const uint64_t seed = a.seed;
     const uint32_t s = ch.s;
 
-    // ---- stage the window: coalesced global loads into this warp's shared-memory slice ----
-    for (int x = lane; x < TW; x += 32) {
-        const int32_t g = contiguous ? static_cast<int32_t>(wstart + x) : wrap_site(wstart + x, L);
-        const int64_t p = ch.offset + g;
-        s_cell[x] = a.in.cell[p];
-        s_off[x] = a.in.off[p];
+    // ---- stage the window in this warp's shared-memory slice ----
+    // Contiguous, 16-byte aligned windows arrive by TMA bulk copies (one per array, completion
+    // on the warp's mbarrier); windows that wrap around the chain or start unaligned use
+    // coalesced read-only loads.
+    const bool tma_in = contiguous && (((ch.offset + wstart) & 3) == 0);
+    if (tma_in) {
+        uint64_t* bar = &s_bar[warp];
+        if (lane == 0) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
+        }
+        __syncwarp();
+        if (lane == 0) {
+            constexpr uint32_t bytes = TW * 4;
+            const int64_t p0 = ch.offset + wstart;
+            mbar_arrive_expect_tx(bar, bytes * (2 + NC));
+            tma_load_1d(s_cell, a.in.cell + p0, bytes, bar);
+            tma_load_1d(s_off, a.in.off + p0, bytes, bar);
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-            s_c[c * TW + x] = a.in.c[c][p];
+            for (int c = 0; c < NC; ++c)
+                tma_load_1d(s_c + c * TW, a.in.c[c] + p0, bytes, bar);
+        }
+        const bool landed = __all_sync(kFull, mbar_wait(bar, 0));   // warp-uniform outcome
+        if (!landed) {
+            // the copy did not land: flag it, give the copies one more bounded wait, drop the tile
+            if (lane == 0)
+                atomicExch(a.error, 1);
+            mbar_wait(bar, 0);
+            return;
+        }
+    } else {
+        const int32_t* __restrict__ g_cell = a.in.cell;
+        const float* __restrict__ g_off = a.in.off;
+        for (int x = lane; x < TW; x += 32) {
+            const int32_t g = contiguous ? static_cast<int32_t>(wstart + x) : wrap_site(wstart + x, L);
+            const int64_t p = ch.offset + g;
+            s_cell[x] = __ldg(g_cell + p);
+            s_off[x] = __ldg(g_off + p);
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                s_c[c * TW + x] = __ldg(a.in.c[c] + p);
+        }
+        __syncwarp();
     }
-    __syncwarp();
 
     int n[S];
     float d[S];
@@ -130,9 +172,14 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
         if constexpr (KIND == kRB)
             rb_coefficients(q[0][j], q[1][j], q[2][j], q[3][j], f, A[j], B[j], C[j]);
     }
+    __syncwarp();   // the staging area is reused by the regeneration queue below
 
     // ---- K Euler steps, all in registers ----
     unsigned n_cross = 0;
+    // per-warp request queue of the cooperative regeneration, in the staging area (idle here)
+    int32_t* q_site = s_cell;
+    int32_t* q_cell = s_cell + 32;
+    float* q_val = s_off;
 #pragma unroll 1
     for (int k = 0; k < K; ++k) {
         const int nl = __shfl_up_sync(kFull, n[S - 1], 1);
@@ -156,8 +203,12 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
             d[j] = dn;
             cross |= out_of_cell(dn) << j;
         }
-        if (cross) {
-            n_cross += __popc(cross);
+        if (__any_sync(kFull, cross)) {
+            // Cell changes.  A one-cell move needs one new disorder value (RF: R(n+1) after an
+            // upward move, R(n) after a downward one; RB: V(n+2) / V(n-1)); the others shift
+            // within the cache.  These requests are evaluated warp-cooperatively below.  A jump
+            // of several cells (rare) regenerates the whole cache of that site in place.
+            unsigned req = 0, up = 0;
 #pragma unroll
             for (int j = 0; j < S; ++j) {
                 if (!((cross >> j) & 1u))
@@ -167,38 +218,92 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
                     continue;
                 const int nn = n[j] + kk;
                 n[j] = nn;
+                ++n_cross;
                 if constexpr (KIND == kNone)
                     continue;
-                const int64_t gx = wstart + lane * S + j;
-                const int32_t i = contiguous ? static_cast<int32_t>(gx) : wrap_site(gx, L);
-                if constexpr (KIND == kRF) {
+                if (kk == 1 || kk == -1) {
+                    req |= 1u << j;
                     if (kk == 1) {
-                        q[0][j] = q[1][j];
-                        q[1][j] = rf_f32(seed, s, i, nn + 1) + f;
-                    } else if (kk == -1) {
-                        q[1][j] = q[0][j];
-                        q[0][j] = rf_f32(seed, s, i, nn) + f;
+                        up |= 1u << j;
+#pragma unroll
+                        for (int c = 0; c + 1 < NC; ++c)
+                            q[c][j] = q[c + 1][j];
                     } else {
-                        q[0][j] = rf_f32(seed, s, i, nn) + f;
-                        q[1][j] = rf_f32(seed, s, i, nn + 1) + f;
+#pragma unroll
+                        for (int c = NC - 1; c > 0; --c)
+                            q[c][j] = q[c - 1][j];
                     }
                 } else {
-                    if (kk == 1) {
-                        q[0][j] = q[1][j];
-                        q[1][j] = q[2][j];
-                        q[2][j] = q[3][j];
-                        q[3][j] = rb_f32(seed, s, i, nn + 2);
-                    } else if (kk == -1) {
-                        q[3][j] = q[2][j];
-                        q[2][j] = q[1][j];
-                        q[1][j] = q[0][j];
-                        q[0][j] = rb_f32(seed, s, i, nn - 1);
+                    const int32_t i = site_index(wstart, lane * S + j, contiguous, L);
+                    if constexpr (KIND == kRF) {
+                        q[0][j] = rf_f32(seed, s, i, nn) + f;
+                        q[1][j] = rf_f32(seed, s, i, nn + 1) + f;
                     } else {
 #pragma unroll
                         for (int c = 0; c < 4; ++c)
                             q[c][j] = rb_f32(seed, s, i, nn - 1 + c);
+                        rb_coefficients(q[0][j], q[1][j], q[2][j], q[3][j], f, A[j], B[j], C[j]);
                     }
-                    rb_coefficients(q[0][j], q[1][j], q[2][j], q[3][j], f, A[j], B[j], C[j]);
+                }
+            }
+            if constexpr (KIND != kNone) {
+                // warp-wide exclusive scan of the request counts -> queue positions
+                const int cnt = __popc(req);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o)
+                        incl += y;
+                }
+                const int total = __shfl_sync(kFull, incl, 31);
+                const int first = incl - cnt;
+                for (int base = 0; base < total; base += 32) {
+                    // enqueue (site, cell) of the requests with positions base .. base+31
+                    int p = first - base;
+#pragma unroll
+                    for (int j = 0; j < S; ++j) {
+                        if ((req >> j) & 1u) {
+                            if (static_cast<unsigned>(p) < 32u) {
+                                q_site[p] = site_index(wstart, lane * S + j, contiguous, L);
+                                // RF: R(n+1) after an up move, R(n) after a down move.
+                                // RB: V(n+2) after an up move, V(n-1) after a down move.
+                                const int off_up = (KIND == kRF) ? 1 : 2;
+                                const int off_dn = (KIND == kRF) ? 0 : -1;
+                                q_cell[p] = n[j] + (((up >> j) & 1u) ? off_up : off_dn);
+                            }
+                            ++p;
+                        }
+                    }
+                    __syncwarp();
+                    if (base + lane < total) {
+                        if constexpr (KIND == kRF)
+                            q_val[lane] = rf_f32(seed, s, q_site[lane], q_cell[lane]) + f;
+                        else
+                            q_val[lane] = rb_f32(seed, s, q_site[lane], q_cell[lane]);
+                    }
+                    __syncwarp();
+                    p = first - base;
+#pragma unroll
+                    for (int j = 0; j < S; ++j) {
+                        if ((req >> j) & 1u) {
+                            if (static_cast<unsigned>(p) < 32u) {
+                                const float v = q_val[p];
+                                if ((up >> j) & 1u)
+                                    q[NC - 1][j] = v;
+                                else
+                                    q[0][j] = v;
+                            }
+                            ++p;
+                        }
+                    }
+                    __syncwarp();
+                }
+                if constexpr (KIND == kRB) {
+#pragma unroll
+                    for (int j = 0; j < S; ++j)
+                        if ((req >> j) & 1u)
+                            rb_coefficients(q[0][j], q[1][j], q[2][j], q[3][j], f, A[j], B[j], C[j]);
                 }
             }
         }
@@ -211,9 +316,11 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
     }
 
     // ---- checkpoint partial sums of the state after the K steps (owned sites only) ----
+    // FP32 sums relative to the warp's reference cell (lane 0's first site; the spread inside a
+    // tile is small), FP32 warp reduction, then one FP64 shift to the chain reference in lane 0.
     if (a.do_obs) {
         const int32_t c_ref = static_cast<int32_t>(a.shift[td.chain]);
-        const int32_t nref = n[0];
+        const int32_t nref = __shfl_sync(kFull, n[0], 0);
         float sF = 0.0f, sy = 0.0f, syy = 0.0f;
         int cnt = 0;
 #pragma unroll
@@ -232,28 +339,27 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
                 ++cnt;
             }
         }
-        const double rel = static_cast<double>(nref) - static_cast<double>(c_ref);
-        double tF = sF;
-        double t1 = static_cast<double>(sy) + cnt * rel;
-        double t2 = static_cast<double>(syy) + 2.0 * rel * static_cast<double>(sy) + cnt * rel * rel;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            tF += __shfl_down_sync(kFull, tF, o);
-            t1 += __shfl_down_sync(kFull, t1, o);
-            t2 += __shfl_down_sync(kFull, t2, o);
+            sF += __shfl_down_sync(kFull, sF, o);
+            sy += __shfl_down_sync(kFull, sy, o);
+            syy += __shfl_down_sync(kFull, syy, o);
+            cnt += __shfl_down_sync(kFull, cnt, o);
         }
         if (lane == 0) {
+            const double rel = static_cast<double>(nref) - static_cast<double>(c_ref);
+            const double dsy = sy;
             double* dst = a.partial + static_cast<size_t>(a.tile_base + tile) * 3;
-            dst[0] = tF;
-            dst[1] = t1;
-            dst[2] = t2;
+            dst[0] = sF;
+            dst[1] = dsy + cnt * rel;
+            dst[2] = static_cast<double>(syy) + rel * (2.0 * dsy + cnt * rel);
         }
     }
 
     if (K == 0)
         return;
 
-    // ---- write the owned sites back: registers -> shared -> coalesced global stores ----
+    // ---- write the owned sites back: registers -> shared -> global ----
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < S; ++j) {
@@ -264,15 +370,32 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
         for (int c = 0; c < NC; ++c)
             s_c[c * TW + x] = q[c][j];
     }
-    __syncwarp();
-    for (int o = lane; o < owned; o += 32) {
-        const int x = o + K;
-        const int64_t p = ch.offset + td.start + o;
-        a.out.cell[p] = s_cell[x];
-        a.out.off[p] = s_off[x];
+    const int64_t out0 = ch.offset + td.start;
+    const bool tma_out = ((K & 3) == 0) && ((out0 & 3) == 0) && ((owned & 3) == 0);
+    if (tma_out) {
+        fence_proxy_async_shared();   // generic-proxy writes above -> visible to the bulk copy
+        __syncwarp();
+        if (lane == 0) {
+            const uint32_t bytes = static_cast<uint32_t>(owned) * 4;
+            tma_store_1d(a.out.cell + out0, s_cell + K, bytes);
+            tma_store_1d(a.out.off + out0, s_off + K, bytes);
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-            a.out.c[c][p] = s_c[c * TW + x];
+            for (int c = 0; c < NC; ++c)
+                tma_store_1d(a.out.c[c] + out0, s_c + c * TW + K, bytes);
+            tma_store_commit();
+            tma_store_wait_all();
+        }
+    } else {
+        __syncwarp();
+        for (int o = lane; o < owned; o += 32) {
+            const int x = o + K;
+            const int64_t p = out0 + o;
+            a.out.cell[p] = s_cell[x];
+            a.out.off[p] = s_off[x];
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                a.out.c[c][p] = s_c[c * TW + x];
+        }
     }
 }
 
