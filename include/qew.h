@@ -179,6 +179,34 @@ int qew_enable_stats(qew_handle h, int32_t enable);
 int qew_get_stats(qew_handle h, int64_t* launches, int64_t* fused_launches, double* fused_ms, int64_t* site_updates,
                   int64_t* crossings);
 
+/*
+ * qew_observe_state_noalloc -- per-chain observables (Eqs. 3-5: v, ubar, w2) of an FP32-split
+ * state that the CALLER holds in device memory, computed without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot let a library
+ * call cudaMalloc -- for instance a framework whose caching allocator already owns the GPU's
+ * memory, or a time-critical loop that must not pay the device-wide synchronisation that
+ * cudaMalloc/cudaFree can cause.  It computes the same quantities as qew_observe_ex does at the
+ * current step of a handle.
+ *   cell, off  DEVICE pointers, batch * L elements each, chain c at offset c * L: the integer cell
+ *              n_i and the FP32 offset d_i in [0, 1) of u_i = n_i + d_i (the layout that
+ *              qew_get_cells / qew_get_state describe).  Chain c has sample index s = c.
+ *   f, disorder_kind, seed  as in qew_create; the pinning force is regenerated from them.
+ *   stream     cudaStream_t to run on (NULL: legacy default stream); synchronised before return.
+ *   v_out, ubar_out, w2_out  HOST pointers to `batch` doubles each, or NULL.
+ * Scratch: a fixed array of 256-byte-aligned device memory inside the library (about 1.7 MB,
+ * held by every GPU that loads the library until the process exits): at most 4096 chains and
+ * 65536 tiles of 256 sites (batch * ceil(L / 256) <= 65536, i.e. up to 2^24 sites); larger
+ * inputs are rejected with QEW_EINVAL.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress), so the first call should come before any stream
+ * capture.  Every call overwrites the part of the array it uses and leaves its contents there;
+ * calls whose work overlaps on the GPU (other streams, other host threads) share the array and
+ * race -- serialise them.  Errors: QEW_EINVAL (bad sizes or pointers), QEW_ECUDA; message via
+ * qew_last_error(NULL).
+ */
+int qew_observe_state_noalloc(const int32_t* cell, const float* off, int64_t L, int32_t batch, double f,
+                              int32_t disorder_kind, uint64_t seed, void* stream, double* v_out,
+                              double* ubar_out, double* w2_out);
+
 /* qew_last_error -- message of the last failed call on `h` (NULL: of the last failed creation
  * or handle-less call on this thread).  Never NULL; "" if there was no error. */
 const char* qew_last_error(qew_handle h);

@@ -779,6 +779,11 @@ int set_state_impl(qew_ctx* h, const double* u_in)
 
 }  // namespace
 
+void qew::set_last_error(const std::string& msg)
+{
+    g_last_error = msg;
+}
+
 extern "C" {
 
 int qew_create(qew_handle* out, int64_t L, int32_t batch, double f, double dt, int32_t disorder_kind, uint64_t seed)

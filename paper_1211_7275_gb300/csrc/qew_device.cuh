@@ -132,6 +132,25 @@ __device__ __forceinline__ double rb_f64(uint64_t seed, uint32_t s, int32_t i, i
     return rb_value_f64(disorder_words(seed, s, i, n, kTagRB));
 }
 
+// Exact int -> float for -2^22 <= k < 2^22 without the conversion pipe: adding the bit pattern
+// of 1.5 * 2^23 places k in the mantissa of a float whose unit in the last place is 1; the
+// subtraction then removes the bias exactly (the "magic number" conversion).
+__device__ __forceinline__ float small_int_to_float(int k)
+{
+    return __int_as_float(k + 0x4B400000) - 12582912.0f;
+}
+
+// RB cubic coefficients of F_p + f = A + d (B + d C) for the Catmull-Rom spline through
+// p0..p3 = V(n-1 .. n+2):  -dV/du = -1/2 [(p2 - p0) + 2 b d + 3 c d^2],
+// b = 2 p0 - 5 p1 + 4 p2 - p3, c = -p0 + 3 p1 - 3 p2 + p3.
+__device__ __forceinline__ void rb_coefficients(float p0, float p1, float p2, float p3, float f, float& A,
+                                                float& B, float& C)
+{
+    A = fmaf(-0.5f, p2 - p0, f);
+    B = -(((2.0f * p0 - 5.0f * p1) + 4.0f * p2) - p3);
+    C = -1.5f * (((3.0f * p1 - p0) - 3.0f * p2) + p3);
+}
+
 // Site index i modulo L for any int64 position (windows may wrap more than once on short chains).
 __device__ __forceinline__ int32_t wrap_site(int64_t g, int32_t L)
 {

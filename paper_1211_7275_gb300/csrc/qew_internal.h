@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "qew_device.cuh"
 
 namespace qew {
@@ -78,6 +80,9 @@ cudaError_t f64_cells(const ChainDesc* chains, const TileDesc* tiles, int32_t n_
 // mass (rounded to an integer cell when `integer_shift`).
 cudaError_t reduce_chains(const ChainDesc* chains, int32_t n_chains, const double* partial, double* shift,
                           double* obs, int integer_shift, cudaStream_t stream);
+
+// Message returned by qew_last_error(NULL) for calls without a handle (this thread).
+void set_last_error(const std::string& msg);
 
 cudaError_t philox_words(const uint32_t* ctr, const uint32_t* key, int64_t n_blocks, uint32_t* out,
                          cudaStream_t stream);

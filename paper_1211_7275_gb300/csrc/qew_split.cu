@@ -28,14 +28,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Exact int -> float for -2^22 <= k < 2^22 without the conversion pipe: adding the bit pattern
-// of 1.5 * 2^23 places k in the mantissa of a float whose unit in the last place is 1; the
-// subtraction then removes the bias exactly (the "magic number" conversion).
-__device__ __forceinline__ float small_int_to_float(int k)
-{
-    return __int_as_float(k + 0x4B400000) - 12582912.0f;
-}
-
 // Offset outside [0, 1) (or NaN / -0): compare the bit pattern; every float in [0, 1) is
 // below the pattern of 1.0f, negative values have the sign bit set.
 __device__ __forceinline__ unsigned out_of_cell(float d)
@@ -57,17 +49,6 @@ __device__ __forceinline__ int renormalise(float& d)
     }
     d = r;
     return k;
-}
-
-// RB cubic coefficients of F_p + f = A + d (B + d C) for the Catmull-Rom spline through
-// p0..p3 = V(n-1 .. n+2):  -dV/du = -1/2 [(p2 - p0) + 2 b d + 3 c d^2],
-// b = 2 p0 - 5 p1 + 4 p2 - p3, c = -p0 + 3 p1 - 3 p2 + p3.
-__device__ __forceinline__ void rb_coefficients(float p0, float p1, float p2, float p3, float f, float& A,
-                                                float& B, float& C)
-{
-    A = fmaf(-0.5f, p2 - p0, f);
-    B = -(((2.0f * p0 - 5.0f * p1) + 4.0f * p2) - p3);
-    C = -1.5f * (((3.0f * p1 - p0) - 3.0f * p2) + p3);
 }
 
 // Chain-local index of window position x (window start wstart).

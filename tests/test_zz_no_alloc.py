@@ -1,0 +1,68 @@
+"""The allocation-free observation entry point, qew_observe_state_noalloc, checked against the
+handle-based qew_observe_ex on the same state.
+
+Some callers cannot let a library call cudaMalloc.  One example is a framework whose caching
+allocator already holds the GPU's memory, where an allocation behind its back can fail or
+fragment the pool.  Another is a time-critical loop that must not take the device-wide
+synchronisation that cudaMalloc/cudaFree can cause.  For them the library computes the
+observables of a state that the caller keeps in device memory, using a fixed scratch array
+inside the library instead of allocating.  Here a handle relaxes a batch of chains and reports
+v, ubar and w2 at its last observation step.  The same state, copied into caller-owned device
+buffers, goes through the allocation-free entry point twice in a row.  Both calls must agree
+with the handle within the tolerances the parity tests use for these observables.  Oversized
+inputs must be rejected.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from qew_workloads import SEED
+
+pytestmark = pytest.mark.gpu
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@pytest.mark.parametrize("kind,f,L,batch", [(0, 0.72057, 5000, 3), (1, 0.90749, 3001, 2), (2, 0.4, 700, 1)])
+def test_noalloc_matches_observe(kind, f, L, batch):
+    torch = pytest.importorskip("torch")
+    import paper_1211_7275_gb300 as q
+    lib = q.load()
+    steps = [0, 37, 300]
+    with q.Relaxation(L, f, kind, dt=0.1, seed=SEED, batch=batch) as r:
+        obs = r.observe(steps)
+        u, _ = r.state()
+        cells = r.cells()
+    off = (u - cells).astype(np.float32)   # exact: u = n + d with d stored in FP32
+    cell_d = torch.from_numpy(np.ascontiguousarray(cells)).cuda()
+    off_d = torch.from_numpy(np.ascontiguousarray(off)).cuda()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        v = np.full(batch, np.nan)
+        ub = np.full(batch, np.nan)
+        w2 = np.full(batch, np.nan)
+        rc = lib.qew_observe_state_noalloc(ctypes.c_void_p(cell_d.data_ptr()), ctypes.c_void_p(off_d.data_ptr()), L,
+                                           batch, f, kind, SEED, ctypes.c_void_p(stream.cuda_stream), _p(v), _p(ub),
+                                           _p(w2))
+        assert rc == 0, lib.qew_last_error(None)
+        np.testing.assert_allclose(v, obs["v"][-1], rtol=0, atol=2e-4)
+        np.testing.assert_allclose(ub, obs["ubar"][-1], rtol=0, atol=2e-5)
+        np.testing.assert_allclose(w2, obs["w2"][-1], rtol=1e-4, atol=1e-6)
+
+
+def test_noalloc_rejects_oversized_input():
+    torch = pytest.importorskip("torch")
+    import paper_1211_7275_gb300 as q
+    lib = q.load()
+    buf = torch.zeros(16, dtype=torch.int32, device="cuda")
+    ptr = ctypes.c_void_p(buf.data_ptr())
+    v = np.zeros(8)
+    # 2^24 + 1 sites in one chain needs one tile more than the fixed scratch holds
+    rc = lib.qew_observe_state_noalloc(ptr, ptr, (1 << 24) + 1, 1, 1.0, 0, SEED, None, _p(v), None, None)
+    assert rc == -1
+    assert b"too large" in lib.qew_last_error(None)
+    rc = lib.qew_observe_state_noalloc(ptr, ptr, 16, 4097, 1.0, 0, SEED, None, _p(v), None, None)
+    assert rc == -1
