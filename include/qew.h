@@ -93,8 +93,9 @@ int qew_set_stream(qew_handle h, void* stream);
 
 /*
  * qew_set_tuning -- launch shape of the fused FP32-split kernel: `tile_w` sites per warp tile
- * (one of 256, 512, 768, 1024), `K` Euler steps per HBM round trip (temporal-block depth,
- * 1 <= K <= tile_w / 4), `tiles_per_cta` warp tiles per thread block (1, 2, 4 or 8).
+ * (32 lanes x an odd number of sites: 224, 480, 736 or 992; random-bond chains 224 or 480),
+ * `K` Euler steps per HBM round trip (temporal-block depth, 1 <= K <= tile_w / 4),
+ * `tiles_per_cta` warp tiles per thread block (1, 2, 4 or 8).
  * Passing 0 for all three asks for the autotuner, which times candidate shapes on the
  * handle's own chains at the next qew_advance/qew_observe without changing their state.
  * Results never depend on the shape beyond FP32 rounding order, which is identical: each

@@ -82,7 +82,7 @@ struct qew_ctx {
     int n_cache = 2;
 
     // launch shape of the fused kernel
-    int S = 16, K = 16, tpc = 4;
+    int S = 15, K = 16, tpc = 4;
     bool autotune_pending = false;
 
     std::vector<ChainDesc> h_chains;
@@ -167,8 +167,8 @@ void free_split(qew_ctx* h)
     for (int b = 0; b < 2; ++b) {
         dev_free(h->sp[b].cell);
         dev_free(h->sp[b].off);
-        for (int c = 0; c < 4; ++c)
-            dev_free(h->sp[b].c[c]);
+        dev_free(h->sp[b].rf);
+        dev_free(h->sp[b].rb);
     }
 }
 
@@ -219,8 +219,10 @@ int alloc_state(qew_ctx* h)
         for (int b = 0; b < 2; ++b) {
             QEW_CUDA(h, dev_alloc(&h->sp[b].cell, N), "allocating the cell array");
             QEW_CUDA(h, dev_alloc(&h->sp[b].off, N), "allocating the offset array");
-            for (int c = 0; c < h->n_cache; ++c)
-                QEW_CUDA(h, dev_alloc(&h->sp[b].c[c], N), "allocating the disorder cache");
+            if (h->kinds_mask & (1 << kRF))
+                QEW_CUDA(h, dev_alloc(&h->sp[b].rf, N), "allocating the RF disorder cache");
+            if (h->kinds_mask & (1 << kRB))
+                QEW_CUDA(h, dev_alloc(&h->sp[b].rb, N), "allocating the RB disorder cache");
         }
     } else {
         free_split(h);
@@ -476,7 +478,7 @@ int autotune(qew_ctx* h)
             return build_layout(h);
         }
     }
-    const int S_all[] = {8, 16, 24, 32};
+    const int S_all[] = {7, 15, 23, 31};
     const int K_all[] = {8, 16, 32};
     const int T_all[] = {2, 4};
     float best = 1e30f;
@@ -595,7 +597,7 @@ int create_impl(qew_handle* out, int32_t n_chains, const int64_t* L, const doubl
         h->seed = seed;
         h->precision = precision;
         if (h->kinds_mask & 2)
-            h->S = 8;
+            h->S = 7;
         rc = build_layout(h);
         if (rc == QEW_OK)
             rc = alloc_state(h);
@@ -842,7 +844,7 @@ int qew_set_tuning(qew_handle h, int32_t tile_w, int32_t K, int32_t tiles_per_ct
         return QEW_OK;
     }
     if (tile_w % 32 != 0)
-        return fail(h, QEW_EINVAL, "tile_w must be a multiple of 32");
+        return fail(h, QEW_EINVAL, "tile_w must be one of 224, 480, 736, 992");
     const int S = tile_w / 32;
     for (int k = 0; k < kNumKinds; ++k)
         if ((h->kinds_mask >> k & 1) && !split_supported(k, S))

@@ -12,11 +12,13 @@
 namespace qew {
 
 // FP32-split state: cell n (int32), in-cell offset d (float, [0,1)) and the disorder cache
-// of each site: RF keeps R(n), R(n+1) in c[0], c[1]; RB keeps V(n-1..n+2) in c[0..3].
+// of each site, interleaved per site: RF keeps (R(n) + f, R(n+1) + f) in rf, RB keeps
+// (V(n-1), V(n), V(n+1), V(n+2)) in rb.  A chain of kind NONE uses neither.
 struct SplitState {
     int32_t* cell;
     float* off;
-    float* c[4];
+    float2* rf;
+    float4* rb;
 };
 
 // FP64 state: displacement u, and the disorder cache of the cell `ncache` it was drawn for:

@@ -7,17 +7,24 @@
 // random values at integer (i, n) (Sec. III.B and the cases of Sec. IV.C); observables of
 // Eqs. 3-5 (Sec. II).
 //
-// State of a site: integer cell n and FP32 offset d in [0, 1) (u = n + d), plus its disorder
-// cache: RF keeps R(n) + f and R(n+1) + f, RB keeps V(n-1 .. n+2).  The drive f is folded into
-// the RF cache so that F_p + f costs one subtraction and one FMA per site-step.
+// State of a site: integer cell n and FP32 offset d in [0, 1) (u = n + d), held in registers,
+// plus its disorder cache, held in shared memory: RF (R(n) + f, R(n+1) + f) -- the drive f is
+// folded in, so F_p + f is one subtraction and one FMA -- and RB V(n-1 .. n+2) with the cubic
+// coefficients of F_p + f beside them.
 //
 // Work decomposition: one warp owns one tile of 32 * S sites of a chain, S consecutive sites
-// per lane held in registers.  A tile advanced K steps needs K extra sites on each side (the
-// stencil's light cone), so the window is [start - K, start - K + 32 S) and the owned sites
+// per lane.  A tile advanced K steps needs K extra sites on each side (the stencil's light
+// cone), so the window is [start - K, start - K + 32 S) and the owned sites
 // [start, start + w_own), w_own <= 32 S - 2K; the outermost sites of the window go stale one
 // per step from each edge and are never stored.  Windows wrap around periodic chains (any
 // number of times for chains shorter than a tile).  Halo exchange inside a step is two warp
-// shuffles per neighbour; there is no shared-memory traffic and no barrier inside the K loop.
+// shuffles per neighbour and there is no block-wide barrier.
+//
+// Cell crossings: the owning lane moves the site to its new cell and appends a request to the
+// warp's queue in shared memory (a shared-memory atomic gives the slot; every request names a
+// different site, so the order does not matter); after the step the warp evaluates the queued
+// Philox values 32 lanes at a time and writes them straight into the shared-memory cache of the
+// requesting sites.
 #include <cstdio>
 
 #include "qew_internal.h"
@@ -36,10 +43,15 @@ __device__ __forceinline__ unsigned out_of_cell(float d)
 }
 
 // Move a site whose offset left [0, 1) to its new cell: returns the cell shift k and leaves
-// d in [0, 1).  A tiny negative offset can round to 1.0f after the shift; then the site stays
-// in the upper cell with d = 0.
+// d in [0, 1).  One-cell upward moves take the exact d - 1 path; anything else goes through
+// floor.  A tiny negative offset can round to 1.0f after the shift; then the site stays in the
+// upper cell with d = 0.
 __device__ __forceinline__ int renormalise(float& d)
 {
+    if (d >= 1.0f && d < 2.0f) {
+        d -= 1.0f;   // exact
+        return 1;
+    }
     const float fk = floorf(d);
     int k = static_cast<int>(fk);
     float r = d - fk;
@@ -51,25 +63,50 @@ __device__ __forceinline__ int renormalise(float& d)
     return k;
 }
 
-// Chain-local index of window position x (window start wstart).
+// Chain-local index of window position x (window start wstart, |wstart| <= K).  A window wraps
+// at most once around a chain at least as long as the window; shorter chains take the modulo.
 __device__ __forceinline__ int32_t site_index(int64_t wstart, int x, bool contiguous, int32_t L)
 {
     const int64_t g = wstart + x;
-    return contiguous ? static_cast<int32_t>(g) : wrap_site(g, L);
+    if (contiguous)
+        return static_cast<int32_t>(g);
+    if (g >= -static_cast<int64_t>(L) && g < 2 * static_cast<int64_t>(L)) {
+        const int32_t r = static_cast<int32_t>(g);
+        return r < 0 ? r + L : (r >= L ? r - L : r);
+    }
+    return wrap_site(g, L);
 }
 
+// Bytes of disorder cache per site in HBM / in shared memory.
 template <int KIND>
-struct CacheWidth {
-    static constexpr int value = (KIND == kRB) ? 4 : 2;
+struct CacheBytes {
+    static constexpr int hbm = (KIND == kRF) ? 8 : (KIND == kRB) ? 16 : 0;
+    static constexpr int smem = (KIND == kRF) ? 8 : (KIND == kRB) ? 32 : 0;
 };
 
+// Queue entry codes (bits 16..17 of the first word; bits 0..15 hold the window position).
+constexpr int kMoveUp = 1;
+constexpr int kMoveDown = 2;
+constexpr int kMoveFar = 3;
+
+// Resident 256-thread blocks per SM asked of the register allocator, per kind and lanes' sites:
+// the largest count for which the kernel still needs no (or almost no) register spills.
 template <int KIND, int S>
-__global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
+struct MinBlocks {
+    static constexpr int value = (S <= 8) ? ((KIND == kRB) ? 3 : 4) : (S <= 16) ? ((KIND == kRB) ? 2 : 3) : 2;
+};
+
+// Sites per lane are odd: lane l reads its cache at word offsets 2 S l (RF) or 4 S l (RB), and
+// an odd S spreads a half-warp (quarter-warp for 16-byte loads) over distinct shared-memory banks.
+
+template <int KIND, int S>
+__global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_kernel(SplitLaunch a)
 {
-    constexpr int NC = CacheWidth<KIND>::value;
     constexpr int TW = 32 * S;
+    constexpr int WARP_SMEM = TW * (8 + CacheBytes<KIND>::smem);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t s_bar[8];
+    __shared__ int s_qlen[8];
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -77,9 +114,13 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
     if (tile >= a.n_tiles)
         return;  // whole warp; the kernel uses no block-wide barrier
 
-    int32_t* s_cell = reinterpret_cast<int32_t*>(smem_raw) + static_cast<size_t>(warp) * TW * (2 + NC);
-    float* s_off = reinterpret_cast<float*>(s_cell + TW);
-    float* s_c = s_off + TW;
+    unsigned char* wsm = smem_raw + static_cast<size_t>(warp) * WARP_SMEM;
+    int32_t* s_cell = reinterpret_cast<int32_t*>(wsm);          // staging of n (load/store)
+    float* s_off = reinterpret_cast<float*>(wsm + 4 * TW);      // staging of d (load/store)
+    int2* s_queue = reinterpret_cast<int2*>(wsm);               // request queue (during the K loop)
+    float2* s_rf = reinterpret_cast<float2*>(wsm + 8 * TW);     // RF cache
+    float4* s_rb = reinterpret_cast<float4*>(wsm + 8 * TW);     // RB values V(n-1..n+2)
+    float4* s_co = reinterpret_cast<float4*>(wsm + 24 * TW);    // RB coefficients (A, B, C, -)
 
     const TileDesc td = a.tiles[tile];
     const ChainDesc ch = a.chains[td.chain];
@@ -106,14 +147,14 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
         }
         __syncwarp();
         if (lane == 0) {
-            constexpr uint32_t bytes = TW * 4;
             const int64_t p0 = ch.offset + wstart;
-            mbar_arrive_expect_tx(bar, bytes * (2 + NC));
-            tma_load_1d(s_cell, a.in.cell + p0, bytes, bar);
-            tma_load_1d(s_off, a.in.off + p0, bytes, bar);
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-                tma_load_1d(s_c + c * TW, a.in.c[c] + p0, bytes, bar);
+            mbar_arrive_expect_tx(bar, TW * (8 + CacheBytes<KIND>::hbm));
+            tma_load_1d(s_cell, a.in.cell + p0, TW * 4, bar);
+            tma_load_1d(s_off, a.in.off + p0, TW * 4, bar);
+            if constexpr (KIND == kRF)
+                tma_load_1d(s_rf, a.in.rf + p0, TW * 8, bar);
+            if constexpr (KIND == kRB)
+                tma_load_1d(s_rb, a.in.rb + p0, TW * 16, bar);
         }
         const bool landed = __all_sync(kFull, mbar_wait(bar, 0));   // warp-uniform outcome
         if (!landed) {
@@ -127,40 +168,38 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
         const int32_t* __restrict__ g_cell = a.in.cell;
         const float* __restrict__ g_off = a.in.off;
         for (int x = lane; x < TW; x += 32) {
-            const int32_t g = contiguous ? static_cast<int32_t>(wstart + x) : wrap_site(wstart + x, L);
-            const int64_t p = ch.offset + g;
+            const int64_t p = ch.offset + site_index(wstart, x, contiguous, L);
             s_cell[x] = __ldg(g_cell + p);
             s_off[x] = __ldg(g_off + p);
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-                s_c[c * TW + x] = __ldg(a.in.c[c] + p);
+            if constexpr (KIND == kRF)
+                s_rf[x] = __ldg(a.in.rf + p);
+            if constexpr (KIND == kRB)
+                s_rb[x] = __ldg(a.in.rb + p);
         }
         __syncwarp();
     }
 
     int n[S];
     float d[S];
-    float q[NC][S];   // RF: R(n)+f, R(n+1)+f.  RB: V(n-1..n+2)
-    float A[KIND == kRB ? S : 1], B[KIND == kRB ? S : 1], C[KIND == kRB ? S : 1];
 #pragma unroll
     for (int j = 0; j < S; ++j) {
         const int x = lane * S + j;
         n[j] = s_cell[x];
         d[j] = s_off[x];
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-            q[c][j] = s_c[c * TW + x];
-        if constexpr (KIND == kRB)
-            rb_coefficients(q[0][j], q[1][j], q[2][j], q[3][j], f, A[j], B[j], C[j]);
+        if constexpr (KIND == kRB) {
+            const float4 p = s_rb[x];
+            float A, B, C;
+            rb_coefficients(p.x, p.y, p.z, p.w, f, A, B, C);
+            s_co[x] = make_float4(A, B, C, 0.0f);
+        }
     }
-    __syncwarp();   // the staging area is reused by the regeneration queue below
+    int* qlen = &s_qlen[warp];
+    if (lane == 0)
+        *qlen = 0;
+    __syncwarp();   // the staging area becomes the request queue below
 
-    // ---- K Euler steps, all in registers ----
+    // ---- K Euler steps: state in registers, cache in shared memory ----
     unsigned n_cross = 0;
-    // per-warp request queue of the cooperative regeneration, in the staging area (idle here)
-    int32_t* q_site = s_cell;
-    int32_t* q_cell = s_cell + 32;
-    float* q_val = s_off;
 #pragma unroll 1
     for (int k = 0; k < K; ++k) {
         const int nl = __shfl_up_sync(kFull, n[S - 1], 1);
@@ -168,130 +207,120 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
         const int nr = __shfl_down_sync(kFull, n[0], 1);
         const float drn = __shfl_down_sync(kFull, d[0], 1);
         float Dm = small_int_to_float(n[0] - nl) + (d[0] - dl);   // u_j - u_{j-1}
-        unsigned cross = 0;
+        unsigned slow = 0;   // sites needing the general renormalisation (rare)
 #pragma unroll
         for (int j = 0; j < S; ++j) {
+            const int x = lane * S + j;
             const int nn = (j + 1 < S) ? n[j + 1] : nr;
             const float dd = (j + 1 < S) ? d[j + 1] : drn;
             const float Dp = small_int_to_float(nn - n[j]) + (dd - d[j]);   // u_{j+1} - u_j
             float g;                                                         // F_p + f
-            if constexpr (KIND == kRB)
-                g = fmaf(d[j], fmaf(d[j], C[j], B[j]), A[j]);
-            else
-                g = fmaf(d[j], q[1][j] - q[0][j], q[0][j]);
-            const float dn = fmaf(dt, (Dp - Dm) + g, d[j]);
+            if constexpr (KIND == kRF) {
+                const float2 q = s_rf[x];
+                g = fmaf(d[j], q.y - q.x, q.x);
+            } else if constexpr (KIND == kRB) {
+                const float4 co = s_co[x];
+                g = fmaf(d[j], fmaf(d[j], co.z, co.y), co.x);
+            } else {
+                g = f;
+            }
+            float dn = fmaf(dt, (Dp - Dm) + g, d[j]);
             Dm = Dp;
-            d[j] = dn;
-            cross |= out_of_cell(dn) << j;
-        }
-        if (__any_sync(kFull, cross)) {
-            // Cell changes.  A one-cell move needs one new disorder value (RF: R(n+1) after an
-            // upward move, R(n) after a downward one; RB: V(n+2) / V(n-1)); the others shift
-            // within the cache.  These requests are evaluated warp-cooperatively below.  A jump
-            // of several cells (rare) regenerates the whole cache of that site in place.
-            unsigned req = 0, up = 0;
-#pragma unroll
-            for (int j = 0; j < S; ++j) {
-                if (!((cross >> j) & 1u))
-                    continue;
-                const int kk = renormalise(d[j]);
-                if (kk == 0)
-                    continue;
-                const int nn = n[j] + kk;
-                n[j] = nn;
-                ++n_cross;
-                if constexpr (KIND == kNone)
-                    continue;
-                if (kk == 1 || kk == -1) {
-                    req |= 1u << j;
-                    if (kk == 1) {
-                        up |= 1u << j;
-#pragma unroll
-                        for (int c = 0; c + 1 < NC; ++c)
-                            q[c][j] = q[c + 1][j];
-                    } else {
-#pragma unroll
-                        for (int c = NC - 1; c > 0; --c)
-                            q[c][j] = q[c - 1][j];
+            if (out_of_cell(dn)) {
+                // one-cell moves are exact: d - 1 for d in [1, 2), d + 1 for d in [-1, 0) unless
+                // it rounds up to 1; anything else (several cells, -0, NaN) goes to the slow pass
+                int kk = 0;
+                float t = dn;
+                if (dn >= 1.0f && dn < 2.0f) {
+                    t = dn - 1.0f;
+                    kk = 1;
+                } else if (dn < 0.0f && dn >= -1.0f) {
+                    t = dn + 1.0f;
+                    kk = (t < 1.0f) ? -1 : 0;
+                }
+                if (kk != 0) {
+                    dn = t;
+                    n[j] += kk;
+                    ++n_cross;
+                    if constexpr (KIND != kNone) {
+                        const int pos = atomicAdd(qlen, 1);
+                        s_queue[pos] = make_int2(x | ((kk == 1 ? kMoveUp : kMoveDown) << 16), n[j]);
                     }
                 } else {
-                    const int32_t i = site_index(wstart, lane * S + j, contiguous, L);
-                    if constexpr (KIND == kRF) {
-                        q[0][j] = rf_f32(seed, s, i, nn) + f;
-                        q[1][j] = rf_f32(seed, s, i, nn + 1) + f;
-                    } else {
+                    slow |= 1u << j;
+                }
+            }
+            d[j] = dn;
+        }
+        if (__any_sync(kFull, slow)) {
+            // rare: several cells at once, a rounding case or a non-finite offset
 #pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            q[c][j] = rb_f32(seed, s, i, nn - 1 + c);
-                        rb_coefficients(q[0][j], q[1][j], q[2][j], q[3][j], f, A[j], B[j], C[j]);
+            for (int j = 0; j < S; ++j) {
+                if ((slow >> j) & 1u) {
+                    const int kk = renormalise(d[j]);
+                    if (kk != 0) {
+                        n[j] += kk;
+                        ++n_cross;
+                        if constexpr (KIND != kNone) {
+                            const int pos = atomicAdd(qlen, 1);
+                            s_queue[pos] = make_int2((lane * S + j) | (kMoveFar << 16), n[j]);
+                        }
                     }
                 }
             }
-            if constexpr (KIND != kNone) {
-                // warp-wide exclusive scan of the request counts -> queue positions
-                const int cnt = __popc(req);
-                int incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o)
-                        incl += y;
-                }
-                const int total = __shfl_sync(kFull, incl, 31);
-                const int first = incl - cnt;
-                for (int base = 0; base < total; base += 32) {
-                    // enqueue (site, cell) of the requests with positions base .. base+31
-                    int p = first - base;
-#pragma unroll
-                    for (int j = 0; j < S; ++j) {
-                        if ((req >> j) & 1u) {
-                            if (static_cast<unsigned>(p) < 32u) {
-                                q_site[p] = site_index(wstart, lane * S + j, contiguous, L);
-                                // RF: R(n+1) after an up move, R(n) after a down move.
-                                // RB: V(n+2) after an up move, V(n-1) after a down move.
-                                const int off_up = (KIND == kRF) ? 1 : 2;
-                                const int off_dn = (KIND == kRF) ? 0 : -1;
-                                q_cell[p] = n[j] + (((up >> j) & 1u) ? off_up : off_dn);
-                            }
-                            ++p;
+        }
+        if constexpr (KIND != kNone) {
+            __syncwarp();
+            const int qn = *qlen;
+            if (qn > 0) {
+                for (int base = 0; base < qn; base += 32) {
+                    if (base + lane < qn) {
+                        const int2 e = s_queue[base + lane];
+                        const int x = e.x & 0xFFFF;
+                        const int code = e.x >> 16;
+                        const int nn = e.y;
+                        const int32_t i = site_index(wstart, x, contiguous, L);
+                        if constexpr (KIND == kRF) {
+                            // one new value: R(n+1) after an up move, R(n) otherwise
+                            const float v = rf_f32(seed, s, i, code == kMoveUp ? nn + 1 : nn) + f;
+                            const float2 o = s_rf[x];
+                            float2 q;
+                            if (code == kMoveUp)
+                                q = make_float2(o.y, v);
+                            else if (code == kMoveDown)
+                                q = make_float2(v, o.x);
+                            else
+                                q = make_float2(v, rf_f32(seed, s, i, nn + 1) + f);
+                            s_rf[x] = q;
+                        } else {
+                            // one new value: V(n+2) after an up move, V(n-1) otherwise
+                            const float v = rb_f32(seed, s, i, code == kMoveUp ? nn + 2 : nn - 1);
+                            const float4 o = s_rb[x];
+                            float4 p;
+                            if (code == kMoveUp)
+                                p = make_float4(o.y, o.z, o.w, v);
+                            else if (code == kMoveDown)
+                                p = make_float4(v, o.x, o.y, o.z);
+                            else
+                                p = make_float4(v, rb_f32(seed, s, i, nn), rb_f32(seed, s, i, nn + 1),
+                                                rb_f32(seed, s, i, nn + 2));
+                            s_rb[x] = p;
+                            float A, B, C;
+                            rb_coefficients(p.x, p.y, p.z, p.w, f, A, B, C);
+                            s_co[x] = make_float4(A, B, C, 0.0f);
                         }
                     }
-                    __syncwarp();
-                    if (base + lane < total) {
-                        if constexpr (KIND == kRF)
-                            q_val[lane] = rf_f32(seed, s, q_site[lane], q_cell[lane]) + f;
-                        else
-                            q_val[lane] = rb_f32(seed, s, q_site[lane], q_cell[lane]);
-                    }
-                    __syncwarp();
-                    p = first - base;
-#pragma unroll
-                    for (int j = 0; j < S; ++j) {
-                        if ((req >> j) & 1u) {
-                            if (static_cast<unsigned>(p) < 32u) {
-                                const float v = q_val[p];
-                                if ((up >> j) & 1u)
-                                    q[NC - 1][j] = v;
-                                else
-                                    q[0][j] = v;
-                            }
-                            ++p;
-                        }
-                    }
-                    __syncwarp();
                 }
-                if constexpr (KIND == kRB) {
-#pragma unroll
-                    for (int j = 0; j < S; ++j)
-                        if ((req >> j) & 1u)
-                            rb_coefficients(q[0][j], q[1][j], q[2][j], q[3][j], f, A[j], B[j], C[j]);
-                }
+                __syncwarp();
+                if (lane == 0)
+                    *qlen = 0;
+                __syncwarp();
             }
         }
     }
 
     if (a.crossings) {
-        unsigned tot = __reduce_add_sync(kFull, n_cross);
+        const unsigned tot = __reduce_add_sync(kFull, n_cross);
         if (lane == 0 && tot)
             atomicAdd(a.crossings, static_cast<unsigned long long>(tot));
     }
@@ -306,13 +335,17 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
         int cnt = 0;
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-            const int o = lane * S + j - K;
+            const int x = lane * S + j;
+            const int o = x - K;
             if (o >= 0 && o < owned) {
-                float g;
-                if constexpr (KIND == kRB)
-                    g = fmaf(d[j], fmaf(d[j], C[j], B[j]), A[j]);
-                else
-                    g = fmaf(d[j], q[1][j] - q[0][j], q[0][j]);
+                float g = f;
+                if constexpr (KIND == kRF) {
+                    const float2 q = s_rf[x];
+                    g = fmaf(d[j], q.y - q.x, q.x);
+                } else if constexpr (KIND == kRB) {
+                    const float4 co = s_co[x];
+                    g = fmaf(d[j], fmaf(d[j], co.z, co.y), co.x);
+                }
                 sF += g - f;
                 const float y = small_int_to_float(n[j] - nref) + d[j];
                 sy += y;
@@ -347,9 +380,6 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
         const int x = lane * S + j;
         s_cell[x] = n[j];
         s_off[x] = d[j];
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-            s_c[c * TW + x] = q[c][j];
     }
     const int64_t out0 = ch.offset + td.start;
     const bool tma_out = ((K & 3) == 0) && ((out0 & 3) == 0) && ((owned & 3) == 0);
@@ -357,12 +387,13 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
         fence_proxy_async_shared();   // generic-proxy writes above -> visible to the bulk copy
         __syncwarp();
         if (lane == 0) {
-            const uint32_t bytes = static_cast<uint32_t>(owned) * 4;
-            tma_store_1d(a.out.cell + out0, s_cell + K, bytes);
-            tma_store_1d(a.out.off + out0, s_off + K, bytes);
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-                tma_store_1d(a.out.c[c] + out0, s_c + c * TW + K, bytes);
+            const uint32_t cnt = static_cast<uint32_t>(owned);
+            tma_store_1d(a.out.cell + out0, s_cell + K, cnt * 4);
+            tma_store_1d(a.out.off + out0, s_off + K, cnt * 4);
+            if constexpr (KIND == kRF)
+                tma_store_1d(a.out.rf + out0, s_rf + K, cnt * 8);
+            if constexpr (KIND == kRB)
+                tma_store_1d(a.out.rb + out0, s_rb + K, cnt * 16);
             tma_store_commit();
             tma_store_wait_all();
         }
@@ -373,9 +404,10 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
             const int64_t p = out0 + o;
             a.out.cell[p] = s_cell[x];
             a.out.off[p] = s_off[x];
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-                a.out.c[c][p] = s_c[c * TW + x];
+            if constexpr (KIND == kRF)
+                a.out.rf[p] = s_rf[x];
+            if constexpr (KIND == kRB)
+                a.out.rb[p] = s_rb[x];
         }
     }
 }
@@ -383,8 +415,7 @@ __global__ void __launch_bounds__(256) split_step_kernel(SplitLaunch a)
 template <int KIND, int S>
 cudaError_t launch_split(int tiles_per_cta, const SplitLaunch& a, cudaStream_t st)
 {
-    constexpr int NC = CacheWidth<KIND>::value;
-    const size_t smem = static_cast<size_t>(tiles_per_cta) * 32 * S * 4 * (2 + NC);
+    const size_t smem = static_cast<size_t>(tiles_per_cta) * 32 * S * (8 + CacheBytes<KIND>::smem);
     auto kern = split_step_kernel<KIND, S>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess)
@@ -424,16 +455,11 @@ __global__ void split_init_kernel(const ChainDesc* chains, const TileDesc* tiles
         }
         st.cell[p] = n;
         st.off[p] = d;
-        if (ch.kind == kRF) {
-            st.c[0][p] = rf_f32(seed, ch.s, i, n) + ch.f32;
-            st.c[1][p] = rf_f32(seed, ch.s, i, n + 1) + ch.f32;
-        } else if (ch.kind == kRB) {
-            for (int c = 0; c < 4; ++c)
-                st.c[c][p] = rb_f32(seed, ch.s, i, n - 1 + c);
-        } else {
-            st.c[0][p] = ch.f32;
-            st.c[1][p] = ch.f32;
-        }
+        if (ch.kind == kRF)
+            st.rf[p] = make_float2(rf_f32(seed, ch.s, i, n) + ch.f32, rf_f32(seed, ch.s, i, n + 1) + ch.f32);
+        else if (ch.kind == kRB)
+            st.rb[p] = make_float4(rb_f32(seed, ch.s, i, n - 1), rb_f32(seed, ch.s, i, n), rb_f32(seed, ch.s, i, n + 1),
+                                   rb_f32(seed, ch.s, i, n + 2));
     }
 }
 
@@ -459,36 +485,36 @@ __global__ void split_to_f64_kernel(const ChainDesc* chains, const TileDesc* til
 bool split_supported(int kind, int S)
 {
     if (kind == kRB)
-        return S == 8 || S == 16;
-    return S == 8 || S == 16 || S == 24 || S == 32;
+        return S == 7 || S == 15;
+    return S == 7 || S == 15 || S == 23 || S == 31;
 }
 
 size_t split_smem_bytes(int kind, int S, int tiles_per_cta)
 {
-    const int nc = (kind == kRB) ? 4 : 2;
-    return static_cast<size_t>(tiles_per_cta) * 32 * S * 4 * (2 + nc);
+    const int cache = (kind == kRF) ? 8 : (kind == kRB) ? 32 : 0;
+    return static_cast<size_t>(tiles_per_cta) * 32 * S * (8 + cache);
 }
 
 cudaError_t split_step(int kind, int S, int tiles_per_cta, const SplitLaunch& a, cudaStream_t st)
 {
     if (kind == kRF) {
         switch (S) {
-        case 8: return launch_split<kRF, 8>(tiles_per_cta, a, st);
-        case 16: return launch_split<kRF, 16>(tiles_per_cta, a, st);
-        case 24: return launch_split<kRF, 24>(tiles_per_cta, a, st);
-        case 32: return launch_split<kRF, 32>(tiles_per_cta, a, st);
+        case 7: return launch_split<kRF, 7>(tiles_per_cta, a, st);
+        case 15: return launch_split<kRF, 15>(tiles_per_cta, a, st);
+        case 23: return launch_split<kRF, 23>(tiles_per_cta, a, st);
+        case 31: return launch_split<kRF, 31>(tiles_per_cta, a, st);
         }
     } else if (kind == kRB) {
         switch (S) {
-        case 8: return launch_split<kRB, 8>(tiles_per_cta, a, st);
-        case 16: return launch_split<kRB, 16>(tiles_per_cta, a, st);
+        case 7: return launch_split<kRB, 7>(tiles_per_cta, a, st);
+        case 15: return launch_split<kRB, 15>(tiles_per_cta, a, st);
         }
     } else {
         switch (S) {
-        case 8: return launch_split<kNone, 8>(tiles_per_cta, a, st);
-        case 16: return launch_split<kNone, 16>(tiles_per_cta, a, st);
-        case 24: return launch_split<kNone, 24>(tiles_per_cta, a, st);
-        case 32: return launch_split<kNone, 32>(tiles_per_cta, a, st);
+        case 7: return launch_split<kNone, 7>(tiles_per_cta, a, st);
+        case 15: return launch_split<kNone, 15>(tiles_per_cta, a, st);
+        case 23: return launch_split<kNone, 23>(tiles_per_cta, a, st);
+        case 31: return launch_split<kNone, 31>(tiles_per_cta, a, st);
         }
     }
     return cudaErrorInvalidValue;

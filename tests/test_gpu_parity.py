@@ -94,7 +94,7 @@ def test_fp64_closed_form(qew):
 # ------------------------------------------------------------------------------------------
 # FP32-split fused path
 # ------------------------------------------------------------------------------------------
-SHAPES = [(512, 16, 4), (256, 8, 2), (1024, 32, 1), (768, 24, 8)]
+SHAPES = [(480, 16, 4), (224, 8, 2), (992, 32, 1), (736, 24, 8), (480, 13, 2)]
 
 
 def _split_check(u, cells, ref_u, tol=1e-4):
@@ -286,8 +286,8 @@ def test_errors(qew):
             r.set_precision(FP64)
         assert e.value.code == -6
         with pytest.raises(qew.QewError):
-            r.set_tuning(500, 8, 4)
+            r.set_tuning(512, 8, 4)
         with pytest.raises(qew.QewError):
-            r.set_tuning(512, 200, 4)
+            r.set_tuning(480, 200, 4)
         r.observe([])
         r.advance(0)
