@@ -139,8 +139,9 @@ int qew_get_cells(qew_handle h, int32_t* cells_out);
 
 /*
  * qew_set_state -- replace the displacement field (FP64, layout of qew_get_state) and set the
- * step counter to 0.  Values must be finite with |u| < 2^30.  The disorder caches are
- * regenerated for the new cells.
+ * step counter to 0.  Values must be finite with |u| < 2^30, and neighbouring sites (periodic)
+ * must differ by less than 2^12 (so that the cells of a warp tile stay exact in FP32).  The
+ * disorder caches are regenerated for the new cells.
  */
 int qew_set_state(qew_handle h, const double* u_in);
 

@@ -355,6 +355,7 @@ SplitLaunch split_args(qew_ctx* h, int kind, int K, int do_obs, SplitState in, S
     a.partial = h->d_partial;
     a.crossings = h->stats_on ? h->d_crossings : nullptr;
     a.error = h->d_error;
+    a.keys = philox_key_schedule(h->seed);
     return a;
 }
 
@@ -761,10 +762,14 @@ int set_state_impl(qew_ctx* h, const double* u_in)
     std::vector<double> shift0(h->n_chains, 0.0);
     for (int32_t c = 0; c < h->n_chains; ++c) {
         double acc = 0.0;
+        const double* uc = u_in + h->offset[c];
         for (int64_t i = 0; i < h->L[c]; ++i) {
-            const double u = u_in[h->offset[c] + i];
+            const double u = uc[i];
             if (!std::isfinite(u) || std::fabs(u) >= 1073741824.0)
                 return fail(h, QEW_EINVAL, "state values must be finite with |u| < 2^30");
+            const double un = uc[i + 1 == h->L[c] ? 0 : i + 1];
+            if (std::isfinite(un) && std::fabs(un - u) >= 4096.0)
+                return fail(h, QEW_EINVAL, "neighbouring displacements must differ by less than 2^12");
             acc += u;
         }
         shift0[c] = std::floor(acc / static_cast<double>(h->L[c]) + 0.5);

@@ -59,6 +59,40 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The ten round keys of a seed, (k0 + r W0, k1 + r W1) for r = 0..9, computed once on the host:
+// passed as kernel parameters they are read from the constant bank as XOR operands, so a block
+// evaluation needs no key additions.
+struct PhiloxKeys {
+    uint32_t k[20];
+};
+
+__host__ __device__ inline PhiloxKeys philox_key_schedule(uint64_t seed)
+{
+    PhiloxKeys ks;
+    uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        ks.k[2 * r] = k0;
+        ks.k[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return ks;
+}
+
+// Philox4x32-10 with a precomputed key schedule (same function as philox4x32_10).
+__device__ __forceinline__ uint4 philox4x32_10_ks(uint4 c, const PhiloxKeys& ks)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
+        const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
+        const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c.y ^ ks.k[2 * r];
+        const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c.w ^ ks.k[2 * r + 1];
+        c = make_uint4(n0, static_cast<uint32_t>(p1), n2, static_cast<uint32_t>(p0));
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint4 disorder_words(uint64_t seed, uint32_t s, int32_t i, int32_t n, uint32_t tag)
 {
     return philox4x32_10(make_uint4(static_cast<uint32_t>(i), static_cast<uint32_t>(n), s, tag),
@@ -120,6 +154,18 @@ __device__ __forceinline__ float rf_f32(uint64_t seed, uint32_t s, int32_t i, in
 __device__ __forceinline__ float rb_f32(uint64_t seed, uint32_t s, int32_t i, int32_t n)
 {
     return rb_value_f32(disorder_words(seed, s, i, n, kTagRB));
+}
+
+__device__ __forceinline__ float rf_f32(const PhiloxKeys& ks, uint32_t s, int32_t i, int32_t n)
+{
+    return rf_value_f32(
+        philox4x32_10_ks(make_uint4(static_cast<uint32_t>(i), static_cast<uint32_t>(n), s, kTagRF), ks));
+}
+
+__device__ __forceinline__ float rb_f32(const PhiloxKeys& ks, uint32_t s, int32_t i, int32_t n)
+{
+    return rb_value_f32(
+        philox4x32_10_ks(make_uint4(static_cast<uint32_t>(i), static_cast<uint32_t>(n), s, kTagRB), ks));
 }
 
 __device__ __forceinline__ double rf_f64(uint64_t seed, uint32_t s, int32_t i, int32_t n)

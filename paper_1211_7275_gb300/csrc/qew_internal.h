@@ -44,6 +44,7 @@ struct SplitLaunch {
     double* partial;         // [n_tiles_total][3]: sum F, sum (u - c), sum (u - c)^2
     unsigned long long* crossings;  // if not null: cell crossings are added here
     int32_t* error;          // set to 1 if a bounded wait on a bulk copy gave up
+    PhiloxKeys keys;         // round keys of `seed`
 };
 
 // Sites per lane of the fused kernel for each supported tile width (tile_w = 32 * S).

@@ -131,7 +131,6 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     const bool contiguous = (wstart >= 0) && (wstart + TW <= L);
     const float f = ch.f32;
     const float dt = a.dt;
-    const uint64_t seed = a.seed;
     const uint32_t s = ch.s;
 
     // ---- stage the window in this warp's shared-memory slice ----
@@ -179,12 +178,16 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
         __syncwarp();
     }
 
-    int n[S];
+    // Cells are carried as exact small floats relative to the warp's reference cell N0 (window
+    // position 0): a neighbour difference is then (c' - c) + (d' - d), three FP32 operations.
+    // Neighbouring displacements differ by less than 2^12, so a tile's cells stay far below 2^24.
+    const int32_t N0 = s_cell[0];
+    float c[S];
     float d[S];
 #pragma unroll
     for (int j = 0; j < S; ++j) {
         const int x = lane * S + j;
-        n[j] = s_cell[x];
+        c[j] = static_cast<float>(s_cell[x] - N0);
         d[j] = s_off[x];
         if constexpr (KIND == kRB) {
             const float4 p = s_rb[x];
@@ -202,19 +205,19 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     unsigned n_cross = 0;
 #pragma unroll 1
     for (int k = 0; k < K; ++k) {
-        const int nl = __shfl_up_sync(kFull, n[S - 1], 1);
+        const float cl = __shfl_up_sync(kFull, c[S - 1], 1);
         const float dl = __shfl_up_sync(kFull, d[S - 1], 1);
-        const int nr = __shfl_down_sync(kFull, n[0], 1);
+        const float cr = __shfl_down_sync(kFull, c[0], 1);
         const float drn = __shfl_down_sync(kFull, d[0], 1);
-        float Dm = small_int_to_float(n[0] - nl) + (d[0] - dl);   // u_j - u_{j-1}
+        float Dm = (c[0] - cl) + (d[0] - dl);   // u_j - u_{j-1}
         unsigned slow = 0;   // sites needing the general renormalisation (rare)
 #pragma unroll
         for (int j = 0; j < S; ++j) {
             const int x = lane * S + j;
-            const int nn = (j + 1 < S) ? n[j + 1] : nr;
+            const float cn = (j + 1 < S) ? c[j + 1] : cr;
             const float dd = (j + 1 < S) ? d[j + 1] : drn;
-            const float Dp = small_int_to_float(nn - n[j]) + (dd - d[j]);   // u_{j+1} - u_j
-            float g;                                                         // F_p + f
+            const float Dp = (cn - c[j]) + (dd - d[j]);   // u_{j+1} - u_j
+            float g;                                       // F_p + f
             if constexpr (KIND == kRF) {
                 const float2 q = s_rf[x];
                 g = fmaf(d[j], q.y - q.x, q.x);
@@ -240,11 +243,13 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                 }
                 if (kk != 0) {
                     dn = t;
-                    n[j] += kk;
-                    ++n_cross;
+                    c[j] += static_cast<float>(kk);
                     if constexpr (KIND != kNone) {
                         const int pos = atomicAdd(qlen, 1);
-                        s_queue[pos] = make_int2(x | ((kk == 1 ? kMoveUp : kMoveDown) << 16), n[j]);
+                        s_queue[pos] = make_int2(x | ((kk == 1 ? kMoveUp : kMoveDown) << 16),
+                                                 N0 + __float2int_rn(c[j]));
+                    } else {
+                        ++n_cross;
                     }
                 } else {
                     slow |= 1u << j;
@@ -259,11 +264,12 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                 if ((slow >> j) & 1u) {
                     const int kk = renormalise(d[j]);
                     if (kk != 0) {
-                        n[j] += kk;
-                        ++n_cross;
+                        c[j] += static_cast<float>(kk);
                         if constexpr (KIND != kNone) {
                             const int pos = atomicAdd(qlen, 1);
-                            s_queue[pos] = make_int2((lane * S + j) | (kMoveFar << 16), n[j]);
+                            s_queue[pos] = make_int2((lane * S + j) | (kMoveFar << 16), N0 + __float2int_rn(c[j]));
+                        } else {
+                            ++n_cross;
                         }
                     }
                 }
@@ -272,6 +278,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
         if constexpr (KIND != kNone) {
             __syncwarp();
             const int qn = *qlen;
+            n_cross += (lane == 0) ? static_cast<unsigned>(qn) : 0u;
             if (qn > 0) {
                 for (int base = 0; base < qn; base += 32) {
                     if (base + lane < qn) {
@@ -282,7 +289,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                         const int32_t i = site_index(wstart, x, contiguous, L);
                         if constexpr (KIND == kRF) {
                             // one new value: R(n+1) after an up move, R(n) otherwise
-                            const float v = rf_f32(seed, s, i, code == kMoveUp ? nn + 1 : nn) + f;
+                            const float v = rf_f32(a.keys, s, i, code == kMoveUp ? nn + 1 : nn) + f;
                             const float2 o = s_rf[x];
                             float2 q;
                             if (code == kMoveUp)
@@ -290,11 +297,11 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                             else if (code == kMoveDown)
                                 q = make_float2(v, o.x);
                             else
-                                q = make_float2(v, rf_f32(seed, s, i, nn + 1) + f);
+                                q = make_float2(v, rf_f32(a.keys, s, i, nn + 1) + f);
                             s_rf[x] = q;
                         } else {
                             // one new value: V(n+2) after an up move, V(n-1) otherwise
-                            const float v = rb_f32(seed, s, i, code == kMoveUp ? nn + 2 : nn - 1);
+                            const float v = rb_f32(a.keys, s, i, code == kMoveUp ? nn + 2 : nn - 1);
                             const float4 o = s_rb[x];
                             float4 p;
                             if (code == kMoveUp)
@@ -302,8 +309,8 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                             else if (code == kMoveDown)
                                 p = make_float4(v, o.x, o.y, o.z);
                             else
-                                p = make_float4(v, rb_f32(seed, s, i, nn), rb_f32(seed, s, i, nn + 1),
-                                                rb_f32(seed, s, i, nn + 2));
+                                p = make_float4(v, rb_f32(a.keys, s, i, nn), rb_f32(a.keys, s, i, nn + 1),
+                                                rb_f32(a.keys, s, i, nn + 2));
                             s_rb[x] = p;
                             float A, B, C;
                             rb_coefficients(p.x, p.y, p.z, p.w, f, A, B, C);
@@ -330,7 +337,6 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     // tile is small), FP32 warp reduction, then one FP64 shift to the chain reference in lane 0.
     if (a.do_obs) {
         const int32_t c_ref = static_cast<int32_t>(a.shift[td.chain]);
-        const int32_t nref = __shfl_sync(kFull, n[0], 0);
         float sF = 0.0f, sy = 0.0f, syy = 0.0f;
         int cnt = 0;
 #pragma unroll
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                     g = fmaf(d[j], fmaf(d[j], co.z, co.y), co.x);
                 }
                 sF += g - f;
-                const float y = small_int_to_float(n[j] - nref) + d[j];
+                const float y = c[j] + d[j];   // u - N0
                 sy += y;
                 syy = fmaf(y, y, syy);
                 ++cnt;
@@ -361,7 +367,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
             cnt += __shfl_down_sync(kFull, cnt, o);
         }
         if (lane == 0) {
-            const double rel = static_cast<double>(nref) - static_cast<double>(c_ref);
+            const double rel = static_cast<double>(N0) - static_cast<double>(c_ref);
             const double dsy = sy;
             double* dst = a.partial + static_cast<size_t>(a.tile_base + tile) * 3;
             dst[0] = sF;
@@ -378,7 +384,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
 #pragma unroll
     for (int j = 0; j < S; ++j) {
         const int x = lane * S + j;
-        s_cell[x] = n[j];
+        s_cell[x] = N0 + __float2int_rn(c[j]);
         s_off[x] = d[j];
     }
     const int64_t out0 = ch.offset + td.start;
