@@ -61,10 +61,30 @@ def parse():
     return p.parse_args()
 
 
+def rank_seed(rank: int) -> int:
+    """Master seed of a rank: every rank relaxes its own independent disorder samples."""
+    return W.SEED + 1000003 * rank
+
+
 def workload(name: str, rank: int):
     p = W.PRESETS[name]
     return dict(name=name, L=p["L"], batch=p["batch"], kind=p["kind"], f=W.preset_f(name), dt=p["dt"],
-                seed=W.SEED + 1000003 * rank)
+                seed=rank_seed(rank))
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The job's time is the slowest rank's (weak scaling: every rank does the same work)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
 
 
 # ------------------------------------------------------------------------------------------
@@ -142,18 +162,21 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_name: str):
-    """DRAM bytes per site-update of the fused kernel from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "fused_split_kernel.traffic.json")
+def profiled_traffic():
+    """DRAM bytes per site per launch of the fused kernel, from the committed ncu summary, if it
+    was captured on the current kernel source; else None.  Traffic is proportional to the sites a
+    launch streams (not to K), so it scales to the bench's launches by their site count."""
+    import re
+    path = os.path.join(ROOT, "profiles", "split_step_kernel_rf_16x2e20.md")
     try:
         with open(path) as fh:
-            rec = json.load(fh)
-    except (OSError, ValueError):
+            text = fh.read()
+    except OSError:
         return None
-    if rec.get("kernel_sha") != kernel_source_hash():
+    m = re.search(r"traffic-record: kernel_sha=(\w+) dram_bytes_per_site_per_launch=([0-9.]+)", text)
+    if not m or m.group(1) != kernel_source_hash():
         return None
-    return rec.get("dram_bytes_per_site_update", {}).get(workload_name)
+    return float(m.group(2))
 
 
 def load_peaks() -> dict:
@@ -203,7 +226,7 @@ def run_reference(args, rank: int, world: int) -> None:
     if rank != 0:
         return
     wl = workload(args.workload, 0)
-    w, n = 1 << 17, 4
+    w, n = 1 << 19, 8
     for _ in range(args.warmup):
         oracle_sample(wl, w, n)
     vals, secs = [], []
@@ -289,13 +312,8 @@ def main() -> None:
     relax.enable_stats(False)
     n_sites = relax.n_sites
     updates = n_sites * args.relax_steps * args.steps
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    total_updates = updates * world
-    value = total_updates / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = job_throughput(updates, world, ms_max)
 
     # ---- roofline of the fused kernel, from its own event-timed launches ----
     peaks = load_peaks()
@@ -312,9 +330,9 @@ def main() -> None:
     bytes_per_su = 2 * (8 + 4 * (2 if kind != 1 else 4)) / K      # state + cache, read + write per K steps
     hbm_achieved = bytes_per_su * su_per_launch / (per_launch_ms / 1e3) / 1e9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    traffic = profiled_traffic(wl["name"])
+    traffic = profiled_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": (traffic * su_per_launch) if traffic else None,
+                "traffic": (traffic * n_sites) if traffic else None,
                 "kernel": "split_step_kernel (fused stencil+pinning+Euler+regeneration, K-step blocked)",
                 "ops_per_site_update": ops_per_su, "crossings_per_site_update": r_cross,
                 "per_launch_ms": per_launch_ms, "site_updates_per_launch": su_per_launch,

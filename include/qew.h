@@ -87,8 +87,8 @@ int qew_create_batch(qew_handle* out, int32_t n_chains, const int64_t* L, const 
 int qew_set_precision(qew_handle h, int32_t precision);
 
 /* qew_set_stream -- issue all further work on `stream` (a cudaStream_t owned by the caller,
- * e.g. torch.cuda.current_stream().cuda_stream); NULL selects the legacy default stream.
- * Drops any captured CUDA graphs. */
+ * e.g. torch.cuda.current_stream().cuda_stream); NULL selects the handle's own non-blocking
+ * stream (the default).  Drops any captured CUDA graph. */
 int qew_set_stream(qew_handle h, void* stream);
 
 /*
@@ -116,7 +116,10 @@ int qew_advance(qew_handle h, int64_t n_steps);
  * w2_out[k * n_chains + c] = w2 of chain c at step steps[k].  Either output may be NULL.
  * n_times == 0 is a no-op.  Returns after the results are in host memory.  On return the
  * chains are at step steps[n_times - 1].  QEW_ENONFINITE if an observable is NaN/Inf (the
- * outputs are still written).
+ * outputs are still written).  The schedule's launches (fused segments, reductions and the copy
+ * to the host) are captured into a CUDA graph the first time and replayed whenever the same
+ * schedule is observed again from the same step (e.g. after qew_reset); not while statistics
+ * are enabled, and not for schedules needing more than 20000 launches.
  */
 int qew_observe(qew_handle h, const int64_t* steps, int32_t n_times, double* v_out, double* w2_out);
 
@@ -208,6 +211,14 @@ int qew_get_stats(qew_handle h, int64_t* launches, int64_t* fused_launches, doub
 int qew_observe_state_noalloc(const int32_t* cell, const float* off, int64_t L, int32_t batch, double f,
                               int32_t disorder_kind, uint64_t seed, void* stream, double* v_out,
                               double* ubar_out, double* w2_out);
+
+/*
+ * qew_selftest_bounded_wait -- exercise the failure path of the bounded device waits: one warp
+ * waits on an mbarrier that nothing completes, gives up after `spin_limit` polls (1 .. 2^22) and
+ * raises the handle's device error flag, which this call reports as QEW_ETIMEOUT (and clears).
+ * Any other status means the failure path is broken.  The handle stays usable afterwards.
+ */
+int qew_selftest_bounded_wait(qew_handle h, int32_t spin_limit);
 
 /* qew_last_error -- message of the last failed call on `h` (NULL: of the last failed creation
  * or handle-less call on this thread).  Never NULL; "" if there was no error. */

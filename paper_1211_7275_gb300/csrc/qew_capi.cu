@@ -118,6 +118,16 @@ struct qew_ctx {
     unsigned long long* d_crossings = nullptr;
     int32_t* d_error = nullptr;   // set by a kernel whose bounded wait gave up
 
+    // stream owned by the handle (used unless the caller sets one) and the captured observation graph
+    cudaStream_t own_stream = nullptr;
+    bool use_graphs = true;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<int64_t> g_steps;
+    int64_t g_step0 = -1, g_step1 = 0;
+    int g_cur0 = -1, g_cur1 = 0;
+    int g_shape[4] = {0, 0, 0, 0};
+    int64_t g_launches = 0, g_fused = 0, g_su = 0;
+
     std::string err;
 };
 
@@ -190,8 +200,21 @@ void free_events(qew_ctx* h)
     h->ev_used = 0;
 }
 
+void drop_graph(qew_ctx* h)
+{
+    if (h->gexec)
+        cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->g_steps.clear();
+    h->g_step0 = -1;
+}
+
 void free_all(qew_ctx* h)
 {
+    drop_graph(h);
+    if (h->own_stream)
+        cudaStreamDestroy(h->own_stream);
+    h->own_stream = nullptr;
     free_events(h);
     dev_free(h->d_crossings);
     dev_free(h->d_error);
@@ -241,6 +264,7 @@ int alloc_state(qew_ctx* h)
 // the partial-sum buffer.
 int build_layout(qew_ctx* h)
 {
+    drop_graph(h);   // captured launches point at the descriptors rebuilt here
     const int32_t tile_w = 32 * h->S;
     h->w_own = tile_w - 2 * h->K;
     std::vector<TileDesc> lists[kNumKinds];
@@ -580,6 +604,11 @@ int create_impl(qew_handle* out, int32_t n_chains, const int64_t* L, const doubl
         return fail(nullptr, QEW_ENOMEM, "host allocation of the handle failed");
     try {
         cudaGetDevice(&h->device);
+        if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return fail(nullptr, QEW_ECUDA, "creating the handle's stream failed");
+        }
+        h->stream = h->own_stream;
         h->n_chains = n_chains;
         h->L.assign(L, L + n_chains);
         h->f.assign(f, f + n_chains);
@@ -647,6 +676,8 @@ int check_device_error(qew_ctx* h)
 
 int ensure_obs(qew_ctx* h, size_t n)
 {
+    if (n > h->obs_cap || n > h->h_obs_cap)
+        drop_graph(h);   // the captured copy-out targets these buffers
     if (n > h->obs_cap) {
         dev_free(h->d_obs);
         QEW_CUDA(h, dev_alloc(&h->d_obs, n), "allocating observation buffer");
@@ -682,13 +713,86 @@ int observe_impl(qew_ctx* h, const int64_t* steps, int32_t n_times, double* v_ou
     int rc = ensure_obs(h, per * n_times);
     if (rc != QEW_OK)
         return rc;
-    for (int32_t k = 0; k < n_times; ++k) {
-        rc = run_to(h, steps[k], h->d_obs + per * k);
+    if (h->autotune_pending && h->precision == QEW_FP32_SPLIT) {
+        rc = autotune(h);   // allocates: never inside a capture
         if (rc != QEW_OK)
             return rc;
     }
-    QEW_CUDA(h, cudaMemcpyAsync(h->h_obs, h->d_obs, per * n_times * sizeof(double), cudaMemcpyDeviceToHost,
-                                h->stream), "copying observables to the host");
+    // launches this schedule needs (a graph is worth it, and stays small, only up to a bound)
+    int64_t n_launch = 0, at = h->step;
+    for (int32_t k = 0; k < n_times; ++k) {
+        const int64_t seg = steps[k] - at;
+        n_launch += (h->precision == QEW_FP32_SPLIT) ? (seg + h->K - 1) / h->K + 2 : seg + 2;
+        at = steps[k];
+    }
+    const int shape[4] = {h->S, h->K, h->tpc, h->precision};
+    const bool graphable = h->use_graphs && !h->stats_on && n_launch <= 20000 && h->stream != nullptr;
+    const bool replay = graphable && h->gexec && h->g_step0 == h->step && h->g_cur0 == h->cur &&
+                        std::memcmp(h->g_shape, shape, sizeof(shape)) == 0 &&
+                        h->g_steps.size() == static_cast<size_t>(n_times) &&
+                        std::equal(h->g_steps.begin(), h->g_steps.end(), steps);
+    if (replay) {
+        QEW_CUDA(h, cudaGraphLaunch(h->gexec, h->stream), "replaying the observation graph");
+        h->step = h->g_step1;
+        h->cur = h->g_cur1;
+        h->f64.u = h->u64[h->cur];
+        h->n_launches += h->g_launches;
+        h->n_fused += h->g_fused;
+        h->n_site_updates += h->g_su;
+    } else {
+        const int64_t step0 = h->step;
+        const int cur0 = h->cur;
+        const int64_t l0 = h->n_launches, f0 = h->n_fused, s0 = h->n_site_updates;
+        bool capturing = false;
+        if (graphable) {
+            drop_graph(h);
+            capturing = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (!capturing)
+                cudaGetLastError();
+        }
+        for (int32_t k = 0; k < n_times && rc == QEW_OK; ++k)
+            rc = run_to(h, steps[k], h->d_obs + per * k);
+        cudaError_t ce = cudaSuccess;
+        if (rc == QEW_OK)
+            ce = cudaMemcpyAsync(h->h_obs, h->d_obs, per * n_times * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (capturing) {
+            cudaGraph_t graph = nullptr;
+            cudaError_t ee = cudaStreamEndCapture(h->stream, &graph);
+            if (rc != QEW_OK || ce != cudaSuccess || ee != cudaSuccess) {
+                if (graph)
+                    cudaGraphDestroy(graph);
+                h->step = step0;   // nothing ran: undo the host-side bookkeeping
+                h->cur = cur0;
+                h->f64.u = h->u64[h->cur];
+                if (rc != QEW_OK)
+                    return rc;
+                return cuda_fail(h, ce != cudaSuccess ? ce : ee, "capturing the observation graph");
+            }
+            ce = cudaGraphInstantiate(&h->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) {
+                h->gexec = nullptr;
+                h->step = step0;
+                h->cur = cur0;
+                h->f64.u = h->u64[h->cur];
+                return cuda_fail(h, ce, "instantiating the observation graph");
+            }
+            h->g_steps.assign(steps, steps + n_times);
+            h->g_step0 = step0;
+            h->g_cur0 = cur0;
+            h->g_step1 = h->step;
+            h->g_cur1 = h->cur;
+            std::memcpy(h->g_shape, shape, sizeof(shape));
+            h->g_launches = h->n_launches - l0;
+            h->g_fused = h->n_fused - f0;
+            h->g_su = h->n_site_updates - s0;
+            QEW_CUDA(h, cudaGraphLaunch(h->gexec, h->stream), "launching the observation graph");
+        } else {
+            if (rc != QEW_OK)
+                return rc;
+            QEW_CUDA(h, ce, "copying observables to the host");
+        }
+    }
     QEW_CUDA(h, cudaStreamSynchronize(h->stream), "running the relaxation");
     if (int rc2 = check_device_error(h))
         return rc2;
@@ -835,7 +939,10 @@ int qew_set_stream(qew_handle h, void* stream)
 {
     if (int rc = check_handle(h))
         return rc;
-    h->stream = static_cast<cudaStream_t>(stream);
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    h->stream = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
     return QEW_OK;
 }
 
@@ -1068,6 +1175,18 @@ int qew_get_stats(qew_handle h, int64_t* launches, int64_t* fused_launches, doub
     h->n_launches = h->n_fused = h->n_site_updates = 0;
     h->ev_used = 0;
     return QEW_OK;
+}
+
+int qew_selftest_bounded_wait(qew_handle h, int32_t spin_limit)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    if (spin_limit < 1 || spin_limit > (1 << 22))
+        return fail(h, QEW_EINVAL, "spin_limit must lie in [1, 2^22]");
+    DeviceGuard g(h->device);
+    QEW_CUDA(h, bounded_wait_selftest(h->d_error, spin_limit, h->stream), "launching the bounded-wait probe");
+    QEW_CUDA(h, cudaStreamSynchronize(h->stream), "running the bounded-wait probe");
+    return check_device_error(h);
 }
 
 const char* qew_last_error(qew_handle h)

@@ -87,6 +87,9 @@ cudaError_t reduce_chains(const ChainDesc* chains, int32_t n_chains, const doubl
 // Message returned by qew_last_error(NULL) for calls without a handle (this thread).
 void set_last_error(const std::string& msg);
 
+// Launch one warp whose mbarrier wait cannot complete; it sets *d_error after spin_limit polls.
+cudaError_t bounded_wait_selftest(int32_t* d_error, int spin_limit, cudaStream_t stream);
+
 cudaError_t philox_words(const uint32_t* ctr, const uint32_t* key, int64_t n_blocks, uint32_t* out,
                          cudaStream_t stream);
 cudaError_t disorder_values(int kind, int fp64, uint64_t seed, uint32_t s, const int64_t* i, const int64_t* n,

@@ -8,6 +8,7 @@
 // one-pass variance keeps its precision.  One block per chain sums its partials in a fixed
 // order, so results are bitwise reproducible from run to run.
 #include "qew_internal.h"
+#include "qew_tma.cuh"
 
 namespace qew {
 namespace {
@@ -74,7 +75,28 @@ __global__ void disorder_values_kernel(int kind, int fp64, uint64_t seed, uint32
     }
 }
 
+// One warp waits on an mbarrier that nothing will ever complete: the bounded wait must give up
+// and record it in `error`, exactly as the fused kernel does when a bulk copy does not land.
+__global__ void bounded_wait_probe(int32_t* error, int limit)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const bool done = __all_sync(0xffffffffu, mbar_wait(&bar, 0, limit));
+    if (!done && threadIdx.x == 0)
+        atomicExch(error, 1);
+}
+
 }  // namespace
+
+cudaError_t bounded_wait_selftest(int32_t* d_error, int spin_limit, cudaStream_t stream)
+{
+    bounded_wait_probe<<<1, 32, 0, stream>>>(d_error, spin_limit);
+    return cudaGetLastError();
+}
 
 cudaError_t reduce_chains(const ChainDesc* chains, int32_t n_chains, const double* partial, double* shift,
                           double* obs, int integer_shift, cudaStream_t stream)

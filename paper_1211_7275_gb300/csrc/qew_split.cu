@@ -423,9 +423,16 @@ cudaError_t launch_split(int tiles_per_cta, const SplitLaunch& a, cudaStream_t s
 {
     const size_t smem = static_cast<size_t>(tiles_per_cta) * 32 * S * (8 + CacheBytes<KIND>::smem);
     auto kern = split_step_kernel<KIND, S>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess)
-        return e;
+    // raise the dynamic shared-memory limit once per kernel and device to the largest shape in use
+    static int s_limit[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && static_cast<int>(smem) > s_limit[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess)
+            return e;
+        s_limit[dev] = static_cast<int>(smem);
+    }
     const int grid = (a.n_tiles + tiles_per_cta - 1) / tiles_per_cta;
     if (grid == 0)
         return cudaSuccess;

@@ -71,11 +71,11 @@ __device__ __forceinline__ void tma_store_wait_all()
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
-// Bounded wait for phase `phase` of `bar`; false if the limit was reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase)
+// Bounded wait for phase `phase` of `bar`; false if `limit` polls did not see it complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int limit = kMbarSpinLimit)
 {
     const uint32_t addr = smem_u32(bar);
-    for (int it = 0; it < kMbarSpinLimit; ++it) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

@@ -291,3 +291,88 @@ def test_errors(qew):
             r.set_tuning(480, 200, 4)
         r.observe([])
         r.advance(0)
+
+
+# ------------------------------------------------------------------------------------------
+# graph replay, failure path
+# ------------------------------------------------------------------------------------------
+def test_graph_replay_is_bitwise_identical(qew):
+    steps = log_spaced_steps(3000, 15)
+    with qew.Relaxation(30000, 0.72057, RF, dt=0.1, seed=SEED, batch=2) as r:
+        first = r.observe(steps)            # captured
+        r.reset()
+        second = r.observe(steps)           # replayed
+        u_replay, _ = r.state()
+        r.reset()
+        r.enable_stats(True)                # statistics switch graphs off: direct launches
+        third = r.observe(steps)
+        st = r.stats()
+        u_direct, _ = r.state()
+    for k in ("v", "ubar", "w2"):
+        assert np.array_equal(first[k], second[k])
+        assert np.array_equal(first[k], third[k])
+    assert np.array_equal(u_replay, u_direct)
+    assert st["fused_launches"] > 0
+
+
+def test_bounded_wait_gives_up_and_reports(qew):
+    lib = qew.load()
+    with qew.Relaxation(1000, 1.0) as r:
+        rc = lib.qew_selftest_bounded_wait(r._h, 4096)
+        assert rc == -4, lib.qew_last_error(r._h)   # QEW_ETIMEOUT
+        out = r.observe([0, 10])                      # the context and the handle still work
+        assert np.all(np.isfinite(out["v"]))
+
+
+# ------------------------------------------------------------------------------------------
+# the other presets at full size, in the launch shape the autotuner picks, sampled sites
+# ------------------------------------------------------------------------------------------
+def _sampled_sites_check(qew, orc, L, f, kind, n_chains, n_steps, picks_per_chain, chains_to_check, tol=1e-4):
+    Ls = np.atleast_1d(L)
+    fs = np.broadcast_to(np.asarray(f, float), Ls.shape)
+    ks = np.broadcast_to(np.asarray(kind, np.int32), Ls.shape)
+    with qew.Relaxation(Ls, fs, ks, dt=0.1, seed=SEED) as r:
+        r.set_tuning(0, 0, 0)
+        obs = r.observe([0, n_steps - 1, n_steps])
+        u, _ = r.state()
+    off = np.concatenate([[0], np.cumsum(Ls)[:-1]])
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for c in chains_to_check:
+        Lc = int(Ls[c])
+        sites = {0, Lc - 1} | set(int(x) for x in rng.integers(0, Lc, picks_per_chain))
+        for i in sorted(sites):
+            w = 1
+            if 2 * n_steps + w > Lc:
+                continue
+            ref_u, _ = orc.lightcone(Lc, c, float(fs[c]), 0.1, int(ks[c]), SEED, i, w, n_steps)
+            err = abs(u[off[c] + i] - ref_u[0])
+            worst = max(worst, err)
+            assert err <= tol, (c, i, err)
+    dub = obs["ubar"][2] - obs["ubar"][1]
+    assert np.all(np.abs(dub - 0.1 * obs["v"][1]) <= 2e-6 * np.maximum(1, np.abs(obs["ubar"][1])))
+    return worst
+
+
+def test_full_size_rf_16x2e20(qew, orc):
+    from qew_workloads import PRESETS, preset_f
+    p = PRESETS["rf_16x2^20"]
+    _sampled_sites_check(qew, orc, [p["L"]] * p["batch"], preset_f("rf_16x2^20"), RF, p["batch"], 1000, 3,
+                         chains_to_check=[0, 7, 15])
+
+
+def test_full_size_rb_1024x2e16(qew, orc):
+    from qew_workloads import PRESETS, preset_f
+    p = PRESETS["rb_1024x2^16"]
+    _sampled_sites_check(qew, orc, [p["L"]] * p["batch"], preset_f("rb_1024x2^16"), RB, p["batch"], 1000, 2,
+                         chains_to_check=[0, 511, 1023])
+
+
+def test_full_size_uneven_256(qew, orc):
+    from qew_workloads import preset_f, sweep_offsets, uneven_kinds, uneven_lengths
+    L = uneven_lengths(256)
+    kinds = uneven_kinds(256)
+    base = np.where(kinds == RF, preset_f("rf_16x2^20"), preset_f("rb_1024x2^16"))
+    f = base * (1.0 + sweep_offsets(256))
+    chains = [int(np.argmin(L)), int(np.argmax(L)), 5, 100, 255]
+    _sampled_sites_check(qew, orc, L, f, kinds, 256, 600, 2, chains_to_check=chains)
