@@ -20,11 +20,12 @@
 // number of times for chains shorter than a tile).  Halo exchange inside a step is two warp
 // shuffles per neighbour and there is no block-wide barrier.
 //
-// Cell crossings: the owning lane moves the site to its new cell and appends a request to the
-// warp's queue in shared memory (a shared-memory atomic gives the slot; every request names a
-// different site, so the order does not matter); after the step the warp evaluates the queued
-// Philox values 32 lanes at a time and writes them straight into the shared-memory cache of the
-// requesting sites.
+// Cell crossings: renormalisation is branch-free (n += floor(d), d -= floor(d)) and leaves one
+// bit per moved site; after the update loop the warp ranks the moved sites with ballots and
+// writes one request per site into its queue in shared memory (no atomics, deterministic order).
+// The queued Philox values are then evaluated 32 lanes at a time and written straight into the
+// shared-memory cache of the requesting sites; the direction of each move is recovered from the
+// cell the cache was drawn for, kept per site in shared memory.
 #include <cstdio>
 
 #include "qew_internal.h"
@@ -34,34 +35,6 @@ namespace qew {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-// Offset outside [0, 1) (or NaN / -0): compare the bit pattern; every float in [0, 1) is
-// below the pattern of 1.0f, negative values have the sign bit set.
-__device__ __forceinline__ unsigned out_of_cell(float d)
-{
-    return __float_as_uint(d) >= 0x3F800000u ? 1u : 0u;
-}
-
-// Move a site whose offset left [0, 1) to its new cell: returns the cell shift k and leaves
-// d in [0, 1).  One-cell upward moves take the exact d - 1 path; anything else goes through
-// floor.  A tiny negative offset can round to 1.0f after the shift; then the site stays in the
-// upper cell with d = 0.
-__device__ __forceinline__ int renormalise(float& d)
-{
-    if (d >= 1.0f && d < 2.0f) {
-        d -= 1.0f;   // exact
-        return 1;
-    }
-    const float fk = floorf(d);
-    int k = static_cast<int>(fk);
-    float r = d - fk;
-    if (r >= 1.0f) {
-        r = 0.0f;
-        k += 1;
-    }
-    d = r;
-    return k;
-}
 
 // Chain-local index of window position x (window start wstart, |wstart| <= K).  A window wraps
 // at most once around a chain at least as long as the window; shorter chains take the modulo.
@@ -77,11 +50,12 @@ __device__ __forceinline__ int32_t site_index(int64_t wstart, int x, bool contig
     return wrap_site(g, L);
 }
 
-// Bytes of disorder cache per site in HBM / in shared memory.
+// Bytes of disorder cache per site in HBM / in shared memory (the shared-memory figure includes
+// the 4-byte cell the cache was drawn for).
 template <int KIND>
 struct CacheBytes {
     static constexpr int hbm = (KIND == kRF) ? 8 : (KIND == kRB) ? 16 : 0;
-    static constexpr int smem = (KIND == kRF) ? 8 : (KIND == kRB) ? 32 : 0;
+    static constexpr int smem = (KIND == kRF) ? 12 : (KIND == kRB) ? 36 : 0;
 };
 
 // Queue entry codes (bits 16..17 of the first word; bits 0..15 hold the window position).
@@ -106,7 +80,6 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     constexpr int WARP_SMEM = TW * (8 + CacheBytes<KIND>::smem);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t s_bar[8];
-    __shared__ int s_qlen[8];
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -121,6 +94,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     float2* s_rf = reinterpret_cast<float2*>(wsm + 8 * TW);     // RF cache
     float4* s_rb = reinterpret_cast<float4*>(wsm + 8 * TW);     // RB values V(n-1..n+2)
     float4* s_co = reinterpret_cast<float4*>(wsm + 24 * TW);    // RB coefficients (A, B, C, -)
+    int32_t* s_ccell = reinterpret_cast<int32_t*>(wsm + (8 + CacheBytes<KIND>::smem - 4) * TW);  // cache's cell
 
     const TileDesc td = a.tiles[tile];
     const ChainDesc ch = a.chains[td.chain];
@@ -189,6 +163,8 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
         const int x = lane * S + j;
         c[j] = static_cast<float>(s_cell[x] - N0);
         d[j] = s_off[x];
+        if constexpr (KIND != kNone)
+            s_ccell[x] = s_cell[x];
         if constexpr (KIND == kRB) {
             const float4 p = s_rb[x];
             float A, B, C;
@@ -196,9 +172,6 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
             s_co[x] = make_float4(A, B, C, 0.0f);
         }
     }
-    int* qlen = &s_qlen[warp];
-    if (lane == 0)
-        *qlen = 0;
     __syncwarp();   // the staging area becomes the request queue below
 
     // ---- K Euler steps: state in registers, cache in shared memory ----
@@ -210,7 +183,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
         const float cr = __shfl_down_sync(kFull, c[0], 1);
         const float drn = __shfl_down_sync(kFull, d[0], 1);
         float Dm = (c[0] - cl) + (d[0] - dl);   // u_j - u_{j-1}
-        unsigned slow = 0;   // sites needing the general renormalisation (rare)
+        unsigned mv = 0;   // sites that changed cell in this step
 #pragma unroll
         for (int j = 0; j < S; ++j) {
             const int x = lane * S + j;
@@ -227,65 +200,43 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
             } else {
                 g = f;
             }
-            float dn = fmaf(dt, (Dp - Dm) + g, d[j]);
+            const float dn = fmaf(dt, (Dp - Dm) + g, d[j]);
             Dm = Dp;
-            if (out_of_cell(dn)) {
-                // one-cell moves are exact: d - 1 for d in [1, 2), d + 1 for d in [-1, 0) unless
-                // it rounds up to 1; anything else (several cells, -0, NaN) goes to the slow pass
-                int kk = 0;
-                float t = dn;
-                if (dn >= 1.0f && dn < 2.0f) {
-                    t = dn - 1.0f;
-                    kk = 1;
-                } else if (dn < 0.0f && dn >= -1.0f) {
-                    t = dn + 1.0f;
-                    kk = (t < 1.0f) ? -1 : 0;
-                }
-                if (kk != 0) {
-                    dn = t;
-                    c[j] += static_cast<float>(kk);
-                    if constexpr (KIND != kNone) {
-                        const int pos = atomicAdd(qlen, 1);
-                        s_queue[pos] = make_int2(x | ((kk == 1 ? kMoveUp : kMoveDown) << 16),
-                                                 N0 + __float2int_rn(c[j]));
-                    } else {
-                        ++n_cross;
-                    }
-                } else {
-                    slow |= 1u << j;
-                }
-            }
-            d[j] = dn;
+            // Branch-free renormalisation.  d - floor(d) is exact; a tiny negative d can round up
+            // to exactly 1, which is a valid representation (the interpolated force is continuous).
+            const float fl = floorf(dn);
+            c[j] += fl;
+            d[j] = dn - fl;
+            mv |= (fl != 0.0f) ? (1u << j) : 0u;
         }
-        if (__any_sync(kFull, slow)) {
-            // rare: several cells at once, a rounding case or a non-finite offset
+        const unsigned anymv = __reduce_or_sync(kFull, mv);
+        if (anymv) {
+            // rank the moved sites with ballots, slot by slot: queue entry = (window position, new cell)
+            int qn = 0;
+            const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
             for (int j = 0; j < S; ++j) {
-                if ((slow >> j) & 1u) {
-                    const int kk = renormalise(d[j]);
-                    if (kk != 0) {
-                        c[j] += static_cast<float>(kk);
-                        if constexpr (KIND != kNone) {
-                            const int pos = atomicAdd(qlen, 1);
-                            s_queue[pos] = make_int2((lane * S + j) | (kMoveFar << 16), N0 + __float2int_rn(c[j]));
-                        } else {
-                            ++n_cross;
-                        }
-                    }
+                if (!((anymv >> j) & 1u))
+                    continue;   // warp-uniform skip
+                const bool m = (mv >> j) & 1u;
+                const unsigned b = __ballot_sync(kFull, m);
+                if constexpr (KIND != kNone) {
+                    if (m)
+                        s_queue[qn + __popc(b & lt)] = make_int2(lane * S + j, N0 + __float2int_rn(c[j]));
                 }
+                qn += __popc(b);
             }
-        }
-        if constexpr (KIND != kNone) {
-            __syncwarp();
-            const int qn = *qlen;
             n_cross += (lane == 0) ? static_cast<unsigned>(qn) : 0u;
-            if (qn > 0) {
+            if constexpr (KIND != kNone) {
+                __syncwarp();
                 for (int base = 0; base < qn; base += 32) {
                     if (base + lane < qn) {
                         const int2 e = s_queue[base + lane];
-                        const int x = e.x & 0xFFFF;
-                        const int code = e.x >> 16;
+                        const int x = e.x;
                         const int nn = e.y;
+                        const int prev = s_ccell[x];
+                        s_ccell[x] = nn;
+                        const int code = (nn == prev + 1) ? kMoveUp : (nn == prev - 1) ? kMoveDown : kMoveFar;
                         const int32_t i = site_index(wstart, x, contiguous, L);
                         if constexpr (KIND == kRF) {
                             // one new value: R(n+1) after an up move, R(n) otherwise
@@ -318,9 +269,6 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                         }
                     }
                 }
-                __syncwarp();
-                if (lane == 0)
-                    *qlen = 0;
                 __syncwarp();
             }
         }
@@ -504,7 +452,7 @@ bool split_supported(int kind, int S)
 
 size_t split_smem_bytes(int kind, int S, int tiles_per_cta)
 {
-    const int cache = (kind == kRF) ? 8 : (kind == kRB) ? 32 : 0;
+    const int cache = (kind == kRF) ? 12 : (kind == kRB) ? 36 : 0;
     return static_cast<size_t>(tiles_per_cta) * 32 * S * (8 + cache);
 }
 
