@@ -81,8 +81,8 @@ struct qew_ctx {
     int kinds_mask = 0;
     int n_cache = 2;
 
-    // launch shape of the fused kernel
-    int S = 15, K = 16, tpc = 4;
+    // launch shape of the fused kernel (defaults: the best measured shapes on a GB300)
+    int S = 23, K = 16, tpc = 2;
     bool autotune_pending = false;
 
     std::vector<ChainDesc> h_chains;
@@ -438,18 +438,25 @@ F64Launch f64_args(qew_ctx* h)
 
 int autotune(qew_ctx* h);
 
+// The autotuner times candidate shapes only once the chains are this many steps past the flat
+// start: the first steps (every site starting to move at once) are not representative.
+constexpr int64_t kTuneAfterSteps = 256;
+
 // Advance to `target` (>= current step); with `obs` record the observables there into obs.
 int run_to(qew_ctx* h, int64_t target, double* obs)
 {
     if (h->precision == QEW_FP32_SPLIT) {
-        if (h->autotune_pending) {
-            int rc = autotune(h);
-            if (rc != QEW_OK)
-                return rc;
-        }
         bool observed = false;
         while (h->step < target) {
-            const int Keff = static_cast<int>(std::min<int64_t>(h->K, target - h->step));
+            if (h->autotune_pending && h->step >= kTuneAfterSteps) {
+                int rc = autotune(h);
+                if (rc != QEW_OK)
+                    return rc;
+            }
+            int64_t seg_end = target;
+            if (h->autotune_pending && h->step < kTuneAfterSteps)
+                seg_end = std::min<int64_t>(target, kTuneAfterSteps);
+            const int Keff = static_cast<int>(std::min<int64_t>(h->K, seg_end - h->step));
             const bool last = (h->step + Keff == target);
             const int do_obs = (obs != nullptr && last) ? 1 : 0;
             int rc = launch_split_all(h, Keff, do_obs, h->sp[h->cur], h->sp[h->cur ^ 1]);
@@ -627,7 +634,7 @@ int create_impl(qew_handle* out, int32_t n_chains, const int64_t* L, const doubl
         h->seed = seed;
         h->precision = precision;
         if (h->kinds_mask & 2)
-            h->S = 7;
+            h->S = 7;   // random-bond caches are larger: 7 sites per lane
         rc = build_layout(h);
         if (rc == QEW_OK)
             rc = alloc_state(h);
@@ -713,7 +720,7 @@ int observe_impl(qew_ctx* h, const int64_t* steps, int32_t n_times, double* v_ou
     int rc = ensure_obs(h, per * n_times);
     if (rc != QEW_OK)
         return rc;
-    if (h->autotune_pending && h->precision == QEW_FP32_SPLIT) {
+    if (h->autotune_pending && h->precision == QEW_FP32_SPLIT && h->step >= kTuneAfterSteps) {
         rc = autotune(h);   // allocates: never inside a capture
         if (rc != QEW_OK)
             return rc;
@@ -726,7 +733,8 @@ int observe_impl(qew_ctx* h, const int64_t* steps, int32_t n_times, double* v_ou
         at = steps[k];
     }
     const int shape[4] = {h->S, h->K, h->tpc, h->precision};
-    const bool graphable = h->use_graphs && !h->stats_on && n_launch <= 20000 && h->stream != nullptr;
+    const bool graphable = h->use_graphs && !h->stats_on && !h->autotune_pending && n_launch <= 20000 &&
+                           h->stream != nullptr;
     const bool replay = graphable && h->gexec && h->g_step0 == h->step && h->g_cur0 == h->cur &&
                         std::memcmp(h->g_shape, shape, sizeof(shape)) == 0 &&
                         h->g_steps.size() == static_cast<size_t>(n_times) &&

@@ -21,8 +21,9 @@
 // shuffles per neighbour and there is no block-wide barrier.
 //
 // Cell crossings: renormalisation is branch-free (n += floor(d), d -= floor(d)) and leaves one
-// bit per moved site; after the update loop the warp ranks the moved sites with ballots and
-// writes one request per site into its queue in shared memory (no atomics, deterministic order).
+// bit per moved site; after the update loop a warp prefix sum of the lanes' move counts places
+// one request per moved site into the warp's queue in shared memory (no atomics, deterministic
+// order).
 // The queued Philox values are then evaluated 32 lanes at a time and written straight into the
 // shared-memory cache of the requesting sites; the direction of each move is recovered from the
 // cell the cache was drawn for, kept per site in shared memory.
@@ -211,20 +212,26 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
         }
         const unsigned anymv = __reduce_or_sync(kFull, mv);
         if (anymv) {
-            // rank the moved sites with ballots, slot by slot: queue entry = (window position, new cell)
-            int qn = 0;
-            const unsigned lt = (1u << lane) - 1u;
+            // queue positions: warp prefix sum of the lanes' move counts, then each lane's moved
+            // sites in slot order (one predicated store per slot, no ballots or atomics); queue
+            // entry = (window position, new cell)
+            const int cnt = __popc(mv);
+            int incl = cnt;
 #pragma unroll
-            for (int j = 0; j < S; ++j) {
-                if (!((anymv >> j) & 1u))
-                    continue;   // warp-uniform skip
-                const bool m = (mv >> j) & 1u;
-                const unsigned b = __ballot_sync(kFull, m);
-                if constexpr (KIND != kNone) {
-                    if (m)
-                        s_queue[qn + __popc(b & lt)] = make_int2(lane * S + j, N0 + __float2int_rn(c[j]));
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            const int qn = __shfl_sync(kFull, incl, 31);
+            const int qbase = incl - cnt;
+            if constexpr (KIND != kNone) {
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    if ((mv >> j) & 1u)
+                        s_queue[qbase + __popc(mv & ((1u << j) - 1u))] =
+                            make_int2(lane * S + j, N0 + __float2int_rn(c[j]));
                 }
-                qn += __popc(b);
             }
             n_cross += (lane == 0) ? static_cast<unsigned>(qn) : 0u;
             if constexpr (KIND != kNone) {
