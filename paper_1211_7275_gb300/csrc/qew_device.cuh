@@ -118,13 +118,17 @@ __device__ __forceinline__ float cos_2pi_word(uint32_t x)
 // FP32: ln U1 is taken as log1p(-(1 - U1)) when U1 > 1/2, where 1 - U1 = (~x0 + 1/2) 2^-32 is
 // exact in the word arithmetic; this keeps the small values of R near U1 -> 1 accurate
 // (rounding U1 itself to FP32 would flush them to zero).
+// One log1pf for both halves, so a warp evaluating many values does not diverge: for U1 < 1/2,
+// U1 = m 2^e with m in [1, 2) read from the float's bits and ln U1 = e ln 2 + log1p(m - 1).
 __device__ __forceinline__ float rf_value_f32(uint4 w)
 {
-    float lg;
-    if (w.x & 0x80000000u)
-        lg = log1pf(-fmaf(static_cast<float>(~w.x), 0x1p-32f, 0x1p-33f));
-    else
-        lg = logf(fmaf(static_cast<float>(w.x), 0x1p-32f, 0x1p-33f));
+    const bool upper = (w.x & 0x80000000u) != 0;
+    const float u1 = fmaf(static_cast<float>(w.x), 0x1p-32f, 0x1p-33f);
+    const uint32_t bits = __float_as_uint(u1);
+    const float m1 = __uint_as_float((bits & 0x007FFFFFu) | 0x3F800000u) - 1.0f;   // exact
+    const float e = static_cast<float>(static_cast<int>(bits >> 23) - 127);
+    const float t = upper ? -fmaf(static_cast<float>(~w.x), 0x1p-32f, 0x1p-33f) : m1;
+    const float lg = fmaf(upper ? 0.0f : e, 0.693147180559945f, log1pf(t));
     return sqrtf(-2.0f * lg) * cos_2pi_word(w.y);
 }
 
