@@ -8,10 +8,12 @@ no fused multiply-add), this module only marshals numpy arrays through ctypes.
 Functions and the passages they follow:
   philox4x32_10      Philox4x32-10 block function (Salmon et al., SC'11); the paper does not
                      name its generator (Sec. III.B), this is the reading used throughout.
-  disorder_values    R(s,i,n) ~ N(0,1) (RF) or V(s,i,n) ~ U(-1,1) (RB) drawn at integer (i,n),
-                     Sec. III.B and the disorder cases of Sec. IV.C.
-  pinning_force      F_p(i,u): linear interpolation of R (RF) or -dV/du of the Catmull-Rom
-                     spline through V (RB), Sec. III.B.
+  disorder_values    R(s,i,n) ~ N(0,1) (RF), V(s,i,n) ~ U(-1,1) (RB) or G(s,i,n) ~ N(0,1)
+                     (Gaussian RB, Cases 1 and 3) drawn at integer (i,n), Sec. III.B and the
+                     disorder cases of Sec. IV.C.
+  pinning_force      F_p(i,u): linear interpolation of R (RF), -dV/du of the Catmull-Rom
+                     spline through V (RB) or G (Case 1), or -dV/du of the linear spline
+                     through G (Case 3), Sec. III.B and Sec. IV.C.
   rb_potential       the RB spline potential itself (spline pins only).
   run                Euler integration of Eq. 1 (eta = c = 1, periodic in x, Sec. III.B) from
                      the flat start (Sec. II) or a given state, with v, ubar, w2 of Eqs. 3-5.
@@ -32,6 +34,8 @@ import numpy as np
 KIND_RF = 0
 KIND_RB = 1
 KIND_NONE = 2
+KIND_RBG_LINEAR = 3   # Case 3: Gaussian potential, linear spline (force constant per cell)
+KIND_RBG_CUBIC = 4    # Case 1: Gaussian potential, Catmull-Rom spline
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qew_oracle.c")
@@ -65,7 +69,8 @@ def _load():
             lib.oracle_pinning_force.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, P, P,
                                                  ctypes.c_int64, P]
             lib.oracle_pinning_force.restype = None
-            lib.oracle_rb_potential.argtypes = [ctypes.c_uint64, ctypes.c_uint32, P, P, ctypes.c_int64, P]
+            lib.oracle_rb_potential.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, P, P,
+                                                ctypes.c_int64, P]
             lib.oracle_rb_potential.restype = None
             lib.oracle_run.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.c_double, ctypes.c_uint64, P, P,
                                        ctypes.c_int32, P, P, P, P, ctypes.c_int32]
@@ -94,7 +99,7 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 
 def disorder_values(kind: int, seed: int, s: int, i, n) -> np.ndarray:
-    """R(s,i,n) for ``kind`` RF, V(s,i,n) for ``kind`` RB, at integer points (i, n)."""
+    """R(s,i,n) for RF, V(s,i,n) for RB, G(s,i,n) for the Gaussian RB kinds, at integer (i, n)."""
     i = np.ascontiguousarray(i, dtype=np.int64).ravel()
     n = np.ascontiguousarray(n, dtype=np.int64).ravel()
     out = np.empty(i.shape[0], np.float64)
@@ -111,12 +116,12 @@ def pinning_force(kind: int, seed: int, s: int, i, u) -> np.ndarray:
     return out
 
 
-def rb_potential(seed: int, s: int, i, u) -> np.ndarray:
-    """Catmull-Rom RB potential V(i, u) of chain ``s``."""
+def rb_potential(seed: int, s: int, i, u, kind: int = KIND_RB) -> np.ndarray:
+    """RB potential V(i, u) of chain ``s``: Catmull-Rom (RB, Case 1) or linear (Case 3)."""
     i = np.ascontiguousarray(i, dtype=np.int64).ravel()
     u = np.ascontiguousarray(u, dtype=np.float64).ravel()
     out = np.empty(i.shape[0], np.float64)
-    _load().oracle_rb_potential(seed, s, _p(i), _p(u), i.shape[0], _p(out))
+    _load().oracle_rb_potential(kind, seed, s, _p(i), _p(u), i.shape[0], _p(out))
     return out
 
 

@@ -17,8 +17,13 @@
  *   disorder cases):
  *     RF (random field, Case 4):  F = (1 - d) R(i, n) + d R(i, n + 1),  R ~ N(0, 1)
  *     RB (random bond, cubic):    F = -dV/du, V the uniform Catmull-Rom spline through
- *                                 V(i, n-1 .. n+2),  V ~ U(-1, 1)
+ *                                 V(i, n-1 .. n+2),  V ~ U(-1, 1)          (Case 2)
  *     NONE:                       F = 0 (disorder-free line; closed-form tests)
+ *     RB-G linear (Case 3):       F = -dV/du of the linear spline through the Gaussian
+ *                                 potential values G(i, n), G(i, n+1):  F = G(n) - G(n+1),
+ *                                 constant inside a cell and discontinuous at the integers
+ *     RB-G cubic (Case 1):        F = -dV/du, V the Catmull-Rom spline through
+ *                                 G(i, n-1 .. n+2),  G ~ N(0, 1)
  *   with n = floor(u), d = u - n.
  *   Observables (Sec. II, Eqs. 3-5): v = f + (1/L) sum_i F_i at the observed state (the
  *   periodic Laplacian sums to zero), ubar = (1/L) sum_i u_i, w2 = (1/L) sum_i (u_i-ubar)^2.
@@ -27,9 +32,11 @@
  * Random numbers (the paper does not say which generator it used; readings chosen here):
  *   Philox4x32-10 of Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as
  *   1, 2, 3" (SC'11), written from that paper's definition: key (lo32(seed), hi32(seed)),
- *   counter (i, (uint32) n, s, tag) with tag 0 for RF forces and 1 for RB potentials.
+ *   counter (i, (uint32) n, s, tag) with tag 0 for RF forces, 1 for uniform RB potentials
+ *   and 2 for Gaussian RB potentials (shared by Cases 1 and 3: the same potential values,
+ *   interpolated two ways).
  *   Uniforms U_k = (x_k + 1/2) 2^-32 from output words x_0, x_1.
- *   R = sqrt(-2 ln U_1) cos(2 pi U_2)   (Box and Muller 1958, cosine branch)
+ *   R, G = sqrt(-2 ln U_1) cos(2 pi U_2)   (Box and Muller 1958, cosine branch)
  *   V = (x_0 + 1/2) 2^-31 - 1.
  *
  * Build: gcc -O2 -std=c11 -fPIC -shared -ffp-contract=off (no fused multiply-add, so the
@@ -46,6 +53,8 @@
 #define QO_RF 0
 #define QO_RB 1
 #define QO_NONE 2
+#define QO_RBG_LINEAR 3
+#define QO_RBG_CUBIC 4
 
 /* ------------------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon et al., SC'11).                                                */
@@ -94,15 +103,29 @@ static void disorder_words(uint64_t seed, uint32_t s, int64_t i, int64_t n, uint
     philox4x32_10(ctr, key, w);
 }
 
-/* RF force value R(s, i, n) ~ N(0, 1): Box-Muller, cosine branch. */
-static double rf_value(uint64_t seed, uint32_t s, int64_t i, int64_t n)
+/* N(0, 1) value from two output words: Box-Muller, cosine branch. */
+static double box_muller(const uint32_t w[4])
 {
-    uint32_t w[4];
-    disorder_words(seed, s, i, n, 0u, w);
     double u1 = ((double)w[0] + 0.5) * 0x1p-32;
     double u2 = ((double)w[1] + 0.5) * 0x1p-32;
     double r = sqrt(-2.0 * log(u1));
     return r * cos(2.0 * M_PI * u2);
+}
+
+/* RF force value R(s, i, n) ~ N(0, 1). */
+static double rf_value(uint64_t seed, uint32_t s, int64_t i, int64_t n)
+{
+    uint32_t w[4];
+    disorder_words(seed, s, i, n, 0u, w);
+    return box_muller(w);
+}
+
+/* Gaussian RB potential value G(s, i, n) ~ N(0, 1) (Cases 1 and 3). */
+static double rbg_value(uint64_t seed, uint32_t s, int64_t i, int64_t n)
+{
+    uint32_t w[4];
+    disorder_words(seed, s, i, n, 2u, w);
+    return box_muller(w);
 }
 
 /* RB potential value V(s, i, n) ~ U(-1, 1). */
@@ -111,6 +134,12 @@ static double rb_value(uint64_t seed, uint32_t s, int64_t i, int64_t n)
     uint32_t w[4];
     disorder_words(seed, s, i, n, 1u, w);
     return ((double)w[0] + 0.5) * 0x1p-31 - 1.0;
+}
+
+/* Potential value at an integer point for the RB kinds. */
+static double potential_value(int kind, uint64_t seed, uint32_t s, int64_t i, int64_t n)
+{
+    return kind == QO_RB ? rb_value(seed, s, i, n) : rbg_value(seed, s, i, n);
 }
 
 /* Pinning force at site i of chain s and displacement u (Sec. III.B, Sec. IV.C). */
@@ -126,29 +155,37 @@ static double pinning_force(int kind, uint64_t seed, uint32_t s, int64_t i, doub
         double r1 = rf_value(seed, s, i, n + 1);
         return (1.0 - d) * r0 + d * r1;
     }
-    /* RB: V(u) on [n, n+1] is the uniform Catmull-Rom cubic through p0..p3 = V(n-1..n+2):
+    if (kind == QO_RBG_LINEAR) {
+        /* V(u) = (1 - d) G(n) + d G(n+1) on [n, n+1), so -dV/du = G(n) - G(n+1) */
+        return rbg_value(seed, s, i, n) - rbg_value(seed, s, i, n + 1);
+    }
+    /* RB / RB-G cubic: V(u) on [n, n+1] is the uniform Catmull-Rom cubic through
+       p0..p3 = V(n-1..n+2):
        V(d) = 1/2 [2 p1 + (p2 - p0) d + (2p0 - 5p1 + 4p2 - p3) d^2 + (-p0 + 3p1 - 3p2 + p3) d^3]
        and F = -dV/du. */
-    double p0 = rb_value(seed, s, i, n - 1);
-    double p1 = rb_value(seed, s, i, n);
-    double p2 = rb_value(seed, s, i, n + 1);
-    double p3 = rb_value(seed, s, i, n + 2);
+    double p0 = potential_value(kind, seed, s, i, n - 1);
+    double p1 = potential_value(kind, seed, s, i, n);
+    double p2 = potential_value(kind, seed, s, i, n + 1);
+    double p3 = potential_value(kind, seed, s, i, n + 2);
     double a = p2 - p0;
     double b = ((2.0 * p0 - 5.0 * p1) + 4.0 * p2) - p3;
     double c = ((3.0 * p1 - p0) - 3.0 * p2) + p3;
     return -0.5 * ((a + 2.0 * b * d) + 3.0 * c * d * d);
 }
 
-/* RB potential itself (used only by the spline pins). */
-static double rb_potential(uint64_t seed, uint32_t s, int64_t i, double u)
+/* The RB potential itself, V(i, u), for the spline pins: Catmull-Rom (RB, RB-G cubic) or
+   linear (RB-G linear). */
+static double rb_potential(int kind, uint64_t seed, uint32_t s, int64_t i, double u)
 {
     double fl = floor(u);
     int64_t n = (int64_t)fl;
     double d = u - fl;
-    double p0 = rb_value(seed, s, i, n - 1);
-    double p1 = rb_value(seed, s, i, n);
-    double p2 = rb_value(seed, s, i, n + 1);
-    double p3 = rb_value(seed, s, i, n + 2);
+    if (kind == QO_RBG_LINEAR)
+        return (1.0 - d) * rbg_value(seed, s, i, n) + d * rbg_value(seed, s, i, n + 1);
+    double p0 = potential_value(kind, seed, s, i, n - 1);
+    double p1 = potential_value(kind, seed, s, i, n);
+    double p2 = potential_value(kind, seed, s, i, n + 1);
+    double p3 = potential_value(kind, seed, s, i, n + 2);
     double a = p2 - p0;
     double b = ((2.0 * p0 - 5.0 * p1) + 4.0 * p2) - p3;
     double c = ((3.0 * p1 - p0) - 3.0 * p2) + p3;
@@ -159,7 +196,9 @@ void oracle_disorder_values(int kind, uint64_t seed, uint32_t s, const int64_t* 
                             int64_t count, double* out)
 {
     for (int64_t k = 0; k < count; ++k)
-        out[k] = (kind == QO_RF) ? rf_value(seed, s, i[k], n[k]) : rb_value(seed, s, i[k], n[k]);
+        out[k] = (kind == QO_RF) ? rf_value(seed, s, i[k], n[k])
+                 : (kind == QO_RB) ? rb_value(seed, s, i[k], n[k])
+                                   : rbg_value(seed, s, i[k], n[k]);
 }
 
 void oracle_pinning_force(int kind, uint64_t seed, uint32_t s, const int64_t* i, const double* u,
@@ -169,11 +208,11 @@ void oracle_pinning_force(int kind, uint64_t seed, uint32_t s, const int64_t* i,
         out[k] = pinning_force(kind, seed, s, i[k], u[k]);
 }
 
-void oracle_rb_potential(uint64_t seed, uint32_t s, const int64_t* i, const double* u, int64_t count,
+void oracle_rb_potential(int kind, uint64_t seed, uint32_t s, const int64_t* i, const double* u, int64_t count,
                          double* out)
 {
     for (int64_t k = 0; k < count; ++k)
-        out[k] = rb_potential(seed, s, i[k], u[k]);
+        out[k] = rb_potential(kind, seed, s, i[k], u[k]);
 }
 
 /* ------------------------------------------------------------------------------------ */

@@ -6,11 +6,15 @@ P2  disorder-free closed form: with F_p = 0 each Fourier mode of the periodic Eu
 P3  the periodic Laplacian sums to zero, so ubar(step+1) - ubar(step) = dt v(step) with
     v = f + <F_p> (Eq. 3, Sec. II).
 P4  Middleton no-passing (Sec. III.B): ordered initial states stay ordered while the Euler map
-    is monotone, 1 - 2 dt + dt dF/du >= 0 at every site.
+    is monotone, 1 - 2 dt + dt dF/du >= 0 at every site.  This needs a continuous force: for
+    the linear-spline random bond (Case 3) the force jumps at the integers and the Euler map is
+    not monotone there, so P4 is not asked of it.
 P7  hand-computed single steps on tiny chains, the degenerate lengths L = 1, 2, 3.
 Spline pins: the RF force interpolates R linearly between integers (Sec. III.B, Case 4 of
     Sec. IV.C); the RB force is minus the derivative of a C^1 cubic spline through V at the
-    integers with the Catmull-Rom tangents (Cases 1-2).
+    integers with the Catmull-Rom tangents (Cases 1-2); the Case 3 force is minus the slope of
+    the linear spline through G, constant inside a cell, and equals the cell average of the
+    Case 1 force through the same G (both potentials take the same values at the integers).
 Observables: ubar, w2 against numpy's mean and population variance (Eqs. 4-5).
 """
 import math
@@ -40,7 +44,8 @@ def test_closed_form_disorder_free(orc, L, k):
         assert abs(out["w2"][0, 0] - A * A / 2) < 1e-12
 
 
-@pytest.mark.parametrize("kind,L,f", [(0, 257, 1.0), (1, 256, 1.9), (0, 5, 0.3), (1, 3, 2.5)])
+@pytest.mark.parametrize("kind,L,f", [(0, 257, 1.0), (1, 256, 1.9), (0, 5, 0.3), (1, 3, 2.5),
+                                       (3, 256, 1.6), (3, 3, 3.0), (4, 255, 1.5)])
 def test_mean_velocity_invariant(orc, kind, L, f):
     steps = list(range(0, 21)) + [100, 101, 500, 501]
     dt = 0.1
@@ -54,7 +59,7 @@ def test_mean_velocity_invariant(orc, kind, L, f):
     assert np.all(out["ubar"][0] == 0.0)
 
 
-@pytest.mark.parametrize("kind,dt,f", [(0, 0.1, 1.0), (1, 0.02, 1.8)])
+@pytest.mark.parametrize("kind,dt,f", [(0, 0.1, 1.0), (1, 0.02, 1.8), (4, 0.01, 1.5)])
 def test_no_passing(orc, kind, dt, f):
     L = 300
     u0 = random_state(L, 0.5, seed=11)
@@ -81,7 +86,7 @@ def test_degenerate_lengths(orc):
     assert np.allclose(out["u"], [0.2, 0.8], rtol=0, atol=1e-15)
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 3, 4])
 def test_first_step_from_flat(orc, kind):
     """From the flat start lap = 0 and d = 0, so u_i(1) = dt (f + F_p(i, 0))."""
     L, f, dt = 97, 0.8, 0.1
@@ -91,6 +96,25 @@ def test_first_step_from_flat(orc, kind):
     assert np.allclose(out["u"], dt * (f + F0), rtol=0, atol=1e-15)
     if kind == 0:
         assert np.array_equal(F0, orc.disorder_values(0, SEED, 4, i, np.zeros(L)))
+    if kind == 3:
+        G0 = orc.disorder_values(3, SEED, 4, i, np.zeros(L))
+        G1 = orc.disorder_values(3, SEED, 4, i, np.ones(L))
+        assert np.array_equal(F0, G0 - G1)
+
+
+def test_case3_two_steps_by_hand_L3(orc):
+    """Case 3 on L = 3, written out: step 1 from flat, then step 2 with the cells floor(u(1))."""
+    f, dt, s = 2.0, 0.1, 1
+    i = np.arange(3)
+    G = {k: orc.disorder_values(3, SEED, s, i, np.full(3, k)) for k in (-2, -1, 0, 1, 2)}
+    u1 = dt * (f + (G[0] - G[1]))
+    n1 = np.floor(u1).astype(int)
+    F1 = np.array([G[n1[j]][j] - G[n1[j] + 1][j] for j in range(3)])
+    lap = np.array([u1[1] + u1[2] - 2 * u1[0], u1[2] + u1[0] - 2 * u1[1], u1[0] + u1[1] - 2 * u1[2]])
+    u2 = u1 + dt * (lap + f + F1)
+    out = orc.run(3, f, dt, 3, SEED, [1, 2], s=[s], want_state=True)
+    assert np.allclose(out["u"], u2, rtol=0, atol=1e-14)
+    assert abs(out["v"][0, 0] - (f + np.mean(G[0] - G[1]))) < 1e-14
 
 
 def test_rf_force_is_linear_interpolation(orc):
@@ -111,28 +135,70 @@ def test_rf_force_is_linear_interpolation(orc):
     assert np.allclose((F[3] - F[0]) / 0.75, R1 - R0, atol=1e-11)
 
 
-def test_rb_spline_pins(orc):
+@pytest.mark.parametrize("kind", [1, 4])
+def test_rb_spline_pins(orc, kind):
     i, n = random_points(2000, 1 << 18, -40, 40, seed=22)
     s = 6
-    V = [orc.disorder_values(1, SEED, s, i, n + k) for k in (-1, 0, 1, 2)]
+    V = [orc.disorder_values(kind, SEED, s, i, n + k) for k in (-1, 0, 1, 2)]
     nf = n.astype(float)
+    tol = 1.0 if kind == 1 else 4.0   # Gaussian values reach |G| ~ 4.5 on 8000 draws
     # the potential interpolates the drawn values at the integers
-    assert np.allclose(orc.rb_potential(SEED, s, i, nf), V[1], atol=1e-15, rtol=0)
-    assert np.allclose(orc.rb_potential(SEED, s, i, nf + 1 - 1e-13), V[2], atol=1e-11, rtol=0)
+    assert np.allclose(orc.rb_potential(SEED, s, i, nf, kind), V[1], atol=1e-15 * tol, rtol=0)
+    assert np.allclose(orc.rb_potential(SEED, s, i, nf + 1 - 1e-13, kind), V[2], atol=1e-11 * tol, rtol=0)
     # Catmull-Rom tangents: F(n) = -(V(n+1) - V(n-1)) / 2, F(n+1-) = -(V(n+2) - V(n)) / 2
-    assert np.allclose(orc.pinning_force(1, SEED, s, i, nf), -(V[2] - V[0]) / 2, atol=1e-15)
-    assert np.allclose(orc.pinning_force(1, SEED, s, i, nf + 1 - 1e-13), -(V[3] - V[1]) / 2, atol=1e-11)
+    assert np.allclose(orc.pinning_force(kind, SEED, s, i, nf), -(V[2] - V[0]) / 2, atol=1e-15 * tol)
+    assert np.allclose(orc.pinning_force(kind, SEED, s, i, nf + 1 - 1e-13), -(V[3] - V[1]) / 2,
+                       atol=1e-11 * tol)
     # the force is quadratic in the cell: 3-point Gauss-Legendre integrates it exactly, and
     # its integral over the cell is -(V(n+1) - V(n))
     x, w = np.polynomial.legendre.leggauss(3)
-    integral = sum(wk * orc.pinning_force(1, SEED, s, i, nf + 0.5 + 0.5 * xk) for xk, wk in zip(x, w)) * 0.5
-    assert np.allclose(integral, -(V[2] - V[1]), atol=1e-14)
+    integral = sum(wk * orc.pinning_force(kind, SEED, s, i, nf + 0.5 + 0.5 * xk) for xk, wk in zip(x, w)) * 0.5
+    assert np.allclose(integral, -(V[2] - V[1]), atol=1e-14 * tol)
     # F = -dV/du inside the cell (central difference of the potential)
     h = 1e-5
     for d in (0.2, 0.5, 0.77):
-        Fd = orc.pinning_force(1, SEED, s, i, nf + d)
-        dV = (orc.rb_potential(SEED, s, i, nf + d + h) - orc.rb_potential(SEED, s, i, nf + d - h)) / (2 * h)
-        assert np.allclose(Fd, -dV, atol=1e-8)
+        Fd = orc.pinning_force(kind, SEED, s, i, nf + d)
+        dV = (orc.rb_potential(SEED, s, i, nf + d + h, kind) - orc.rb_potential(SEED, s, i, nf + d - h, kind)) / (2 * h)
+        assert np.allclose(Fd, -dV, atol=1e-8 * tol)
+
+
+def test_case3_linear_spline_pins(orc):
+    """Case 3: V is the straight line through G(n), G(n+1) on each cell, F = -dV/du."""
+    i, n = random_points(2000, 1 << 18, -40, 40, seed=23)
+    s = 2
+    G0 = orc.disorder_values(3, SEED, s, i, n)
+    G1 = orc.disorder_values(3, SEED, s, i, n + 1)
+    nf = n.astype(float)
+    # nodes, and the straight line in between
+    assert np.array_equal(orc.rb_potential(SEED, s, i, nf, 3), G0)
+    for d in (0.25, 0.5, 0.9):
+        assert np.allclose(orc.rb_potential(SEED, s, i, nf + d, 3), G0 + d * (G1 - G0), atol=1e-14)
+    # constant inside the cell (including the node itself: floor(n) = n)
+    F = [orc.pinning_force(3, SEED, s, i, nf + d) for d in (0.0, 0.3, 0.75, 1 - 1e-12)]
+    for Fd in F[1:]:
+        assert np.array_equal(Fd, F[0])
+    # minus the slope: the potential falls where the force is positive
+    h = 1e-4
+    dV = (orc.rb_potential(SEED, s, i, nf + 0.5 + h, 3) - orc.rb_potential(SEED, s, i, nf + 0.5 - h, 3)) / (2 * h)
+    assert np.allclose(F[0], -dV, atol=1e-9)
+    # the jump at the upper node is the next cell's force
+    above = orc.pinning_force(3, SEED, s, i, nf + 1.0)
+    G2 = orc.disorder_values(3, SEED, s, i, n + 2)
+    assert np.array_equal(above, G1 - G2)
+
+
+def test_case1_cell_average_is_case3_force(orc):
+    """The cubic (Case 1) and linear (Case 3) splines through the same G agree at the integers,
+    so the Case 1 force averaged over a cell equals the constant Case 3 force of that cell."""
+    i, n = random_points(3000, 1 << 20, -60, 60, seed=24)
+    s = 9
+    nf = n.astype(float)
+    x, w = np.polynomial.legendre.leggauss(3)
+    avg = sum(wk * orc.pinning_force(4, SEED, s, i, nf + 0.5 + 0.5 * xk) for xk, wk in zip(x, w)) * 0.5
+    F3 = orc.pinning_force(3, SEED, s, i, nf + 0.5)
+    assert np.allclose(avg, F3, atol=1e-13, rtol=0)
+    # and the two forces are different functions: the cubic one varies inside the cell
+    assert np.mean(np.abs(orc.pinning_force(4, SEED, s, i, nf + 0.1) - F3) > 1e-3) > 0.9
 
 
 def test_observables_match_numpy(orc):
@@ -146,7 +212,7 @@ def test_observables_match_numpy(orc):
     assert abs(out["v"][0, 0] - (f + np.mean(F))) < 1e-13
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 3, 4])
 def test_lightcone_equals_periodic_run(orc, kind):
     L, n, w = 101, 20, 7
     full = orc.run(L, 1.2, 0.1, kind, SEED, [n], s=[3], want_state=True)["u"]

@@ -7,10 +7,12 @@ and counter (lo32(B >> 16), lo32(B >> 48), B mod 2^16, 0) (established by search
 counters), so arbitrary keys and counter words 0-2 are exercised; word 3 enters the first
 round exactly like word 1 and is exercised from the second round on.
 
-The transforms to R ~ N(0,1) (random field) and V ~ U(-1,1) (random bond) are pinned by
-their distributions (Kolmogorov-Smirnov against scipy), their independence across the
-integer lattice (i, n), and by which output word decides what (sign of R from word 1, V
-increasing in word 0).  The paper fixes only the distributions (Sec. II, Sec. IV.C).
+The transforms to R ~ N(0,1) (random field), V ~ U(-1,1) (random bond) and G ~ N(0,1)
+(Gaussian random-bond potential of Cases 1 and 3, counter tag 2) are pinned by their
+distributions (Kolmogorov-Smirnov against scipy), their independence across the integer
+lattice (i, n), and by which output word of which counter decides what (sign of R and G from
+word 1, magnitude from word 0, V increasing in word 0).  The paper fixes only the
+distributions (Sec. II, Sec. IV.C).
 """
 import ctypes
 import ctypes.util
@@ -95,7 +97,18 @@ def test_rb_values_uniform(orc):
     assert ks.pvalue > 1e-3, ks
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+def test_gaussian_rb_values_standard_normal(orc):
+    i, n = random_points(200_000, 1 << 25, -50, 5000, seed=8)
+    g = orc.disorder_values(orc.KIND_RBG_LINEAR, 12117275, 3, i, n)
+    ks = scipy_stats.kstest(g, "norm")
+    assert ks.pvalue > 1e-3, ks
+    assert abs(g.mean()) < 5 / np.sqrt(g.size)
+    assert abs(g.var() - 1.0) < 0.02
+    # Cases 1 and 3 interpolate the same potential values
+    assert np.array_equal(g, orc.disorder_values(orc.KIND_RBG_CUBIC, 12117275, 3, i, n))
+
+
+@pytest.mark.parametrize("kind", [0, 1, 3])
 def test_values_uncorrelated_on_lattice(orc, kind):
     m = 50_000
     i, n = random_points(m, 1 << 20, -1000, 1000, seed=3)
@@ -106,12 +119,14 @@ def test_values_uncorrelated_on_lattice(orc, kind):
         assert abs(rho) < 5 / np.sqrt(m), (di, dn, ds, rho)
 
 
-def test_rf_sign_follows_word1(orc):
-    """R = sqrt(-2 ln U1) cos(2 pi U2) is positive exactly when U2 lies in the outer quarters."""
+@pytest.mark.parametrize("kind,tag", [(0, 0), (3, 2)])
+def test_gauss_sign_follows_word1(orc, kind, tag):
+    """R = sqrt(-2 ln U1) cos(2 pi U2) is positive exactly when U2 lies in the outer quarters
+    (U1, U2 from the block of counter tag 0 for R, tag 2 for G)."""
     seed, s = 424242, 5
     i, n = random_points(100_000, 1 << 22, -300, 300, seed=4)
-    r = orc.disorder_values(orc.KIND_RF, seed, s, i, n)
-    w = _words(orc, seed, s, i, n, 0)
+    r = orc.disorder_values(kind, seed, s, i, n)
+    w = _words(orc, seed, s, i, n, tag)
     x1 = w[:, 1].astype(np.uint64)
     inner = (x1 >= (1 << 30)) & (x1 < 3 * (1 << 30))
     far = np.abs(x1.astype(np.int64) - (1 << 30)) > 64
@@ -119,12 +134,13 @@ def test_rf_sign_follows_word1(orc):
     assert np.all((r[far] < 0) == inner[far])
 
 
-def test_rf_magnitude_follows_word0(orc):
+@pytest.mark.parametrize("kind,tag", [(0, 0), (3, 2)])
+def test_gauss_magnitude_follows_word0(orc, kind, tag):
     """Among points with the same cosine factor, |R| decreases as word 0 (U1) grows."""
     seed, s = 31337, 1
     i, n = random_points(400_000, 1 << 22, -300, 300, seed=5)
-    r = orc.disorder_values(orc.KIND_RF, seed, s, i, n)
-    w = _words(orc, seed, s, i, n, 0)
+    r = orc.disorder_values(kind, seed, s, i, n)
+    w = _words(orc, seed, s, i, n, tag)
     # cos(2 pi U2) ~ 1 when word 1 is within 2^24 of 0 or 2^32
     sel = (w[:, 1] < (1 << 24)) | (w[:, 1] > 0xFFFFFFFF - (1 << 24))
     x0 = w[sel, 0]
