@@ -8,15 +8,21 @@
  * the explicit Euler method,
  *     u_i <- u_i + dt (u_{i+1} + u_{i-1} - 2 u_i + f + F_p(i, u_i))       (Eq. 1, eta = c = 1)
  * all forces taken from the old state.  The pinning force is built from random numbers drawn
- * at the integer points (i, n) of the (x, u) plane and interpolated in u (Sec. III.B):
- *     QEW_RF_GAUSS_LINEAR        F_p = (1 - d) R(i, n) + d R(i, n + 1),  R ~ N(0, 1)
+ * at the integer points (i, n) of the (x, u) plane and interpolated in u (Sec. III.B; the cases
+ * of Sec. IV.C):
+ *     QEW_RF_GAUSS_LINEAR        F_p = (1 - d) R(i, n) + d R(i, n + 1),  R ~ N(0, 1)  (Case 4)
  *     QEW_RB_UNIFORM_CATMULLROM  F_p = -dV/du, V the Catmull-Rom spline through
- *                                V(i, n - 1 .. n + 2),  V ~ U(-1, 1)
+ *                                V(i, n - 1 .. n + 2),  V ~ U(-1, 1)               (Case 2)
  *     QEW_NONE                   F_p = 0 (disorder-free line)
+ *     QEW_RB_GAUSS_LINEAR        F_p = -dV/du, V the linear spline through G(i, n), G(i, n + 1):
+ *                                F_p = G(i, n) - G(i, n + 1), constant inside a cell and
+ *                                discontinuous at the integers; G ~ N(0, 1)        (Case 3)
+ *     QEW_RB_GAUSS_CATMULLROM    F_p = -dV/du, V the Catmull-Rom spline through
+ *                                G(i, n - 1 .. n + 2)                              (Case 1)
  * with n = floor(u), d = u - n.  The random numbers come from Philox4x32-10 (Salmon et al.,
- * SC'11) with key (lo32(seed), hi32(seed)) and counter (i, (uint32) n, s, tag), tag 0 for R
- * and 1 for V, regenerated on the device whenever a site changes cell (the "memory-free"
- * disorder of Sec. IV.D).  Observables (Eqs. 3-5), per chain: v = f + (1/L) sum_i F_p(i, u_i)
+ * SC'11) with key (lo32(seed), hi32(seed)) and counter (i, (uint32) n, s, tag), tag 0 for R,
+ * 1 for V and 2 for G (the two Gaussian random-bond kinds interpolate the same G), regenerated
+ * on the device whenever a site changes cell (the "memory-free" disorder of Sec. IV.D).  Observables (Eqs. 3-5), per chain: v = f + (1/L) sum_i F_p(i, u_i)
  * (the mean velocity, since the periodic Laplacian sums to zero), ubar = (1/L) sum_i u_i and
  * w2 = (1/L) sum_i (u_i - ubar)^2.
  *
@@ -56,7 +62,9 @@ enum qew_status {
 enum qew_disorder {
     QEW_RF_GAUSS_LINEAR = 0,
     QEW_RB_UNIFORM_CATMULLROM = 1,
-    QEW_NONE = 2
+    QEW_NONE = 2,
+    QEW_RB_GAUSS_LINEAR = 3,
+    QEW_RB_GAUSS_CATMULLROM = 4
 };
 
 enum qew_precision {
@@ -158,8 +166,9 @@ int qew_num_sites(qew_handle h, int64_t* n_sites);
 
 /*
  * qew_disorder_values -- the device generator's disorder values, for validation: for each
- * k < count, out[k] = R(s, i[k], n[k]) (kind QEW_RF_GAUSS_LINEAR) or V(s, i[k], n[k])
- * (QEW_RB_UNIFORM_CATMULLROM), computed on the current device in the arithmetic of
+ * k < count, out[k] = R(s, i[k], n[k]) (kind QEW_RF_GAUSS_LINEAR), V(s, i[k], n[k])
+ * (QEW_RB_UNIFORM_CATMULLROM) or G(s, i[k], n[k]) (QEW_RB_GAUSS_LINEAR and
+ * QEW_RB_GAUSS_CATMULLROM; QEW_NONE is rejected), computed on the current device in the arithmetic of
  * `precision` (FP32 values are widened to double).  Host pointers; synchronous.
  */
 int qew_disorder_values(int32_t kind, int32_t precision, uint64_t seed, uint32_t s, const int64_t* i,

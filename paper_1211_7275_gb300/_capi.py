@@ -21,6 +21,8 @@ QEW_ESTATE = -6
 RF_GAUSS_LINEAR = 0
 RB_UNIFORM_CATMULLROM = 1
 NONE = 2
+RB_GAUSS_LINEAR = 3
+RB_GAUSS_CATMULLROM = 4
 
 FP32_SPLIT = 0
 FP64 = 1

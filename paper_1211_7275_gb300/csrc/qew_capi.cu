@@ -28,9 +28,11 @@ namespace {
 
 thread_local std::string g_last_error;
 
+static_assert(QEW_RF_GAUSS_LINEAR == kRF && QEW_RB_UNIFORM_CATMULLROM == kRB && QEW_NONE == kNone &&
+                  QEW_RB_GAUSS_LINEAR == kRBGLinear && QEW_RB_GAUSS_CATMULLROM == kRBGCubic,
+              "the C ABI's disorder kinds index the kernels' kind table");
 constexpr int32_t kBlockTile = 1024;   // sites per block tile (FP64 path, init, conversions)
 constexpr int64_t kMaxSites = int64_t(1) << 40;
-constexpr int kNumKinds = 3;
 
 struct DeviceGuard {
     int prev = -1;
@@ -87,9 +89,9 @@ struct qew_ctx {
 
     std::vector<ChainDesc> h_chains;
     ChainDesc* d_chains = nullptr;
-    TileDesc* d_tiles[kNumKinds] = {nullptr, nullptr, nullptr};
-    int32_t n_tiles[kNumKinds] = {0, 0, 0};
-    int32_t tile_base[kNumKinds] = {0, 0, 0};
+    TileDesc* d_tiles[kNumKinds] = {};
+    int32_t n_tiles[kNumKinds] = {};
+    int32_t tile_base[kNumKinds] = {};
     int32_t w_own = 0;
     TileDesc* d_btiles = nullptr;
     int32_t n_btiles = 0;
@@ -108,7 +110,7 @@ struct qew_ctx {
     size_t h_obs_cap = 0;
 
     // statistics (qew_enable_stats / qew_get_stats)
-    int64_t sites_of_kind[kNumKinds] = {0, 0, 0};
+    int64_t sites_of_kind[kNumKinds] = {};
     bool stats_on = false;
     int64_t n_launches = 0;
     int64_t n_fused = 0;
@@ -242,10 +244,10 @@ int alloc_state(qew_ctx* h)
         for (int b = 0; b < 2; ++b) {
             QEW_CUDA(h, dev_alloc(&h->sp[b].cell, N), "allocating the cell array");
             QEW_CUDA(h, dev_alloc(&h->sp[b].off, N), "allocating the offset array");
-            if (h->kinds_mask & (1 << kRF))
-                QEW_CUDA(h, dev_alloc(&h->sp[b].rf, N), "allocating the RF disorder cache");
-            if (h->kinds_mask & (1 << kRB))
-                QEW_CUDA(h, dev_alloc(&h->sp[b].rb, N), "allocating the RB disorder cache");
+            if (h->kinds_mask & kPairMask)
+                QEW_CUDA(h, dev_alloc(&h->sp[b].rf, N), "allocating the two-node disorder cache");
+            if (h->kinds_mask & kQuadMask)
+                QEW_CUDA(h, dev_alloc(&h->sp[b].rb, N), "allocating the four-node disorder cache");
         }
     } else {
         free_split(h);
@@ -348,10 +350,10 @@ int init_state(qew_ctx* h, const double* d_u_in, const std::vector<double>& shif
     h->step = 0;
     if (h->precision == QEW_FP32_SPLIT) {
         QEW_CUDA(h, split_init(h->d_chains, h->n_chains, h->d_btiles, h->n_btiles, kBlockTile, h->sp[0], h->seed,
-                               h->kinds_mask & 2, d_u_in, h->stream), "launching the state initialisation");
+                               h->kinds_mask & kQuadMask, d_u_in, h->stream), "launching the state initialisation");
     } else {
         h->f64.u = h->u64[0];
-        QEW_CUDA(h, f64_init(h->d_chains, h->d_btiles, h->n_btiles, kBlockTile, h->f64, h->seed, h->kinds_mask & 2,
+        QEW_CUDA(h, f64_init(h->d_chains, h->d_btiles, h->n_btiles, kBlockTile, h->f64, h->seed, h->kinds_mask & kQuadMask,
                              d_u_in, h->stream), "launching the FP64 state initialisation");
     }
     h->n_launches += 1;
@@ -529,7 +531,7 @@ int autotune(qew_ctx* h)
             if (4 * K > 32 * S)
                 continue;
             for (int T : T_all) {
-                if (split_smem_bytes((h->kinds_mask & 2) ? kRB : kRF, S, T) > 200 * 1024)
+                if (split_smem_bytes((h->kinds_mask & kQuadMask) ? kRB : kRF, S, T) > 200 * 1024)
                     continue;
                 h->S = S;
                 h->K = K;
@@ -600,7 +602,7 @@ int create_impl(qew_handle* out, int32_t n_chains, const int64_t* L, const doubl
             return fail(nullptr, QEW_EINVAL, "chain length " + std::to_string(L[c]) + " outside [1, 2^31)");
         if (!std::isfinite(f[c]))
             return fail(nullptr, QEW_EINVAL, "drive f must be finite");
-        if (kind[c] < QEW_RF_GAUSS_LINEAR || kind[c] > QEW_NONE)
+        if (kind[c] < QEW_RF_GAUSS_LINEAR || kind[c] > QEW_RB_GAUSS_CATMULLROM)
             return fail(nullptr, QEW_EINVAL, "unknown disorder kind " + std::to_string(kind[c]));
         total += L[c];
         if (total >= kMaxSites)
@@ -629,12 +631,12 @@ int create_impl(qew_handle* out, int32_t n_chains, const int64_t* L, const doubl
             h->sites_of_kind[kind[c]] += L[c];
         }
         h->n_sites = off;
-        h->n_cache = (h->kinds_mask & 2) ? 4 : 2;
+        h->n_cache = (h->kinds_mask & kQuadMask) ? 4 : 2;
         h->dt = dt;
         h->seed = seed;
         h->precision = precision;
-        if (h->kinds_mask & 2)
-            h->S = 7;   // random-bond caches are larger: 7 sites per lane
+        if (h->kinds_mask & kQuadMask)
+            h->S = 7;   // four-node caches are larger: 7 sites per lane
         rc = build_layout(h);
         if (rc == QEW_OK)
             rc = alloc_state(h);
@@ -973,7 +975,7 @@ int qew_set_tuning(qew_handle h, int32_t tile_w, int32_t K, int32_t tiles_per_ct
         return fail(h, QEW_EINVAL, "K must lie in [1, tile_w / 4]");
     if (tiles_per_cta != 1 && tiles_per_cta != 2 && tiles_per_cta != 4 && tiles_per_cta != 8)
         return fail(h, QEW_EINVAL, "tiles_per_cta must be 1, 2, 4 or 8");
-    if (split_smem_bytes((h->kinds_mask & 2) ? kRB : kRF, S, tiles_per_cta) > 227 * 1024)
+    if (split_smem_bytes((h->kinds_mask & kQuadMask) ? kRB : kRF, S, tiles_per_cta) > 227 * 1024)
         return fail(h, QEW_EINVAL, "tile_w * tiles_per_cta needs more shared memory than a block has");
     h->S = S;
     h->K = K;
@@ -1077,8 +1079,8 @@ int qew_num_sites(qew_handle h, int64_t* n_sites)
 int qew_disorder_values(int32_t kind, int32_t precision, uint64_t seed, uint32_t s, const int64_t* i,
                         const int64_t* n, int64_t count, double* out)
 {
-    if (kind != QEW_RF_GAUSS_LINEAR && kind != QEW_RB_UNIFORM_CATMULLROM)
-        return fail(nullptr, QEW_EINVAL, "kind must be QEW_RF_GAUSS_LINEAR or QEW_RB_UNIFORM_CATMULLROM");
+    if (kind < QEW_RF_GAUSS_LINEAR || kind > QEW_RB_GAUSS_CATMULLROM || kind == QEW_NONE)
+        return fail(nullptr, QEW_EINVAL, "kind must name a disorder (not QEW_NONE)");
     if (precision != QEW_FP32_SPLIT && precision != QEW_FP64)
         return fail(nullptr, QEW_EINVAL, "unknown precision");
     if (count < 0 || (count > 0 && (!i || !n || !out)))

@@ -13,12 +13,24 @@
 
 namespace qew {
 
-constexpr int kRF = 0;
-constexpr int kRB = 1;
-constexpr int kNone = 2;
+// Disorder kinds (the cases of Sec. IV.C).
+constexpr int kRF = 0;         // random field: Gaussian R at the integers, linear interpolation (Case 4)
+constexpr int kRB = 1;         // random bond: uniform V, Catmull-Rom spline (Case 2)
+constexpr int kNone = 2;       // no disorder
+constexpr int kRBGLinear = 3;  // random bond: Gaussian G, linear spline, F = G(n) - G(n+1) (Case 3)
+constexpr int kRBGCubic = 4;   // random bond: Gaussian G, Catmull-Rom spline (Case 1)
+constexpr int kNumKinds = 5;
 
-constexpr uint32_t kTagRF = 0u;  // counter word 3 of random-field force values
-constexpr uint32_t kTagRB = 1u;  // counter word 3 of random-bond potential values
+// Cache families: "pair" kinds keep the two nodes of the current cell per site, "quad" kinds
+// the four nodes V(n-1 .. n+2) of the cubic spline.
+__host__ __device__ constexpr bool pair_kind(int k) { return k == kRF || k == kRBGLinear; }
+__host__ __device__ constexpr bool quad_kind(int k) { return k == kRB || k == kRBGCubic; }
+constexpr int kPairMask = (1 << kRF) | (1 << kRBGLinear);
+constexpr int kQuadMask = (1 << kRB) | (1 << kRBGCubic);
+
+constexpr uint32_t kTagRF = 0u;   // counter word 3 of random-field force values
+constexpr uint32_t kTagRB = 1u;   // counter word 3 of uniform random-bond potential values
+constexpr uint32_t kTagRBG = 2u;  // counter word 3 of Gaussian random-bond potential values (Cases 1, 3)
 
 // One chain of the batch.
 struct ChainDesc {
@@ -114,13 +126,16 @@ __device__ __forceinline__ float cos_2pi_word(uint32_t x)
     return fmaf(-s, pl, fmaf(-0.5f * pl, pl * c, c));
 }
 
-// R = sqrt(-2 ln U1) cos(2 pi U2), U_k = (x_k + 1/2) 2^-32 (Box-Muller, cosine branch).
+// N(0, 1) value sqrt(-2 ln U1) cos(2 pi U2), U_k = (x_k + 1/2) 2^-32 (Box-Muller, cosine
+// branch): the random-field force R and the Gaussian random-bond potential G.
 // FP32: ln U1 is taken as log1p(-(1 - U1)) when U1 > 1/2, where 1 - U1 = (~x0 + 1/2) 2^-32 is
 // exact in the word arithmetic; this keeps the small values of R near U1 -> 1 accurate
 // (rounding U1 itself to FP32 would flush them to zero).
 // One log1pf for both halves, so a warp evaluating many values does not diverge: for U1 < 1/2,
 // U1 = m 2^e with m in [1, 2) read from the float's bits and ln U1 = e ln 2 + log1p(m - 1).
-__device__ __forceinline__ float rf_value_f32(uint4 w)
+// The value plus `add` is rounded once (the random-field cache holds R + f), by an explicit fused
+// multiply-add, so every kernel that draws a value rounds it the same way.
+__device__ __forceinline__ float gauss_value_plus_f32(uint4 w, float add)
 {
     const bool upper = (w.x & 0x80000000u) != 0;
     const float u1 = fmaf(static_cast<float>(w.x), 0x1p-32f, 0x1p-33f);
@@ -129,10 +144,15 @@ __device__ __forceinline__ float rf_value_f32(uint4 w)
     const float e = static_cast<float>(static_cast<int>(bits >> 23) - 127);
     const float t = upper ? -fmaf(static_cast<float>(~w.x), 0x1p-32f, 0x1p-33f) : m1;
     const float lg = fmaf(upper ? 0.0f : e, 0.693147180559945f, log1pf(t));
-    return sqrtf(-2.0f * lg) * cos_2pi_word(w.y);
+    return __fmaf_rn(sqrtf(-2.0f * lg), cos_2pi_word(w.y), add);
 }
 
-__device__ __forceinline__ double rf_value_f64(uint4 w)
+__device__ __forceinline__ float gauss_value_f32(uint4 w)
+{
+    return gauss_value_plus_f32(w, 0.0f);
+}
+
+__device__ __forceinline__ double gauss_value_f64(uint4 w)
 {
     const double u1 = (static_cast<double>(w.x) + 0.5) * 0x1p-32;
     const double u2 = (static_cast<double>(w.y) + 0.5) * 0x1p-32;
@@ -152,7 +172,18 @@ __device__ __forceinline__ double rb_value_f64(uint4 w)
 
 __device__ __forceinline__ float rf_f32(uint64_t seed, uint32_t s, int32_t i, int32_t n)
 {
-    return rf_value_f32(disorder_words(seed, s, i, n, kTagRF));
+    return gauss_value_f32(disorder_words(seed, s, i, n, kTagRF));
+}
+
+// R(i, n) + f, rounded once: the random-field cache value.
+__device__ __forceinline__ float rf_plus_f32(uint64_t seed, uint32_t s, int32_t i, int32_t n, float f)
+{
+    return gauss_value_plus_f32(disorder_words(seed, s, i, n, kTagRF), f);
+}
+
+__device__ __forceinline__ float rbg_f32(uint64_t seed, uint32_t s, int32_t i, int32_t n)
+{
+    return gauss_value_f32(disorder_words(seed, s, i, n, kTagRBG));
 }
 
 __device__ __forceinline__ float rb_f32(uint64_t seed, uint32_t s, int32_t i, int32_t n)
@@ -162,8 +193,14 @@ __device__ __forceinline__ float rb_f32(uint64_t seed, uint32_t s, int32_t i, in
 
 __device__ __forceinline__ float rf_f32(const PhiloxKeys& ks, uint32_t s, int32_t i, int32_t n)
 {
-    return rf_value_f32(
+    return gauss_value_f32(
         philox4x32_10_ks(make_uint4(static_cast<uint32_t>(i), static_cast<uint32_t>(n), s, kTagRF), ks));
+}
+
+__device__ __forceinline__ float rbg_f32(const PhiloxKeys& ks, uint32_t s, int32_t i, int32_t n)
+{
+    return gauss_value_f32(
+        philox4x32_10_ks(make_uint4(static_cast<uint32_t>(i), static_cast<uint32_t>(n), s, kTagRBG), ks));
 }
 
 __device__ __forceinline__ float rb_f32(const PhiloxKeys& ks, uint32_t s, int32_t i, int32_t n)
@@ -174,7 +211,34 @@ __device__ __forceinline__ float rb_f32(const PhiloxKeys& ks, uint32_t s, int32_
 
 __device__ __forceinline__ double rf_f64(uint64_t seed, uint32_t s, int32_t i, int32_t n)
 {
-    return rf_value_f64(disorder_words(seed, s, i, n, kTagRF));
+    return gauss_value_f64(disorder_words(seed, s, i, n, kTagRF));
+}
+
+__device__ __forceinline__ double rbg_f64(uint64_t seed, uint32_t s, int32_t i, int32_t n)
+{
+    return gauss_value_f64(disorder_words(seed, s, i, n, kTagRBG));
+}
+
+// The two cell nodes of a pair kind (FP32): R + f for RF (the drive is folded into the cache), G
+// for the linear-spline random bond.
+template <int KIND>
+__device__ __forceinline__ float pair_node_f32(const PhiloxKeys& ks, uint32_t s, int32_t i, int32_t n, float f)
+{
+    if constexpr (KIND == kRF)
+        return gauss_value_plus_f32(
+            philox4x32_10_ks(make_uint4(static_cast<uint32_t>(i), static_cast<uint32_t>(n), s, kTagRF), ks), f);
+    else
+        return rbg_f32(ks, s, i, n);
+}
+
+// A spline node of a quad kind (FP32): uniform V or Gaussian G.
+template <int KIND>
+__device__ __forceinline__ float quad_node_f32(const PhiloxKeys& ks, uint32_t s, int32_t i, int32_t n)
+{
+    if constexpr (KIND == kRB)
+        return rb_f32(ks, s, i, n);
+    else
+        return rbg_f32(ks, s, i, n);
 }
 
 __device__ __forceinline__ double rb_f64(uint64_t seed, uint32_t s, int32_t i, int32_t n)
@@ -193,12 +257,15 @@ __device__ __forceinline__ float small_int_to_float(int k)
 // RB cubic coefficients of F_p + f = A + d (B + d C) for the Catmull-Rom spline through
 // p0..p3 = V(n-1 .. n+2):  -dV/du = -1/2 [(p2 - p0) + 2 b d + 3 c d^2],
 // b = 2 p0 - 5 p1 + 4 p2 - p3, c = -p0 + 3 p1 - 3 p2 + p3.
+// Every operation is an explicit round-to-nearest intrinsic: left to itself the compiler may
+// contract a multiply and an add differently in different kernel instantiations, and the cache
+// coefficients (hence the trajectory) would then depend on the launch shape.
 __device__ __forceinline__ void rb_coefficients(float p0, float p1, float p2, float p3, float f, float& A,
                                                 float& B, float& C)
 {
-    A = fmaf(-0.5f, p2 - p0, f);
-    B = -(((2.0f * p0 - 5.0f * p1) + 4.0f * p2) - p3);
-    C = -1.5f * (((3.0f * p1 - p0) - 3.0f * p2) + p3);
+    A = __fmaf_rn(-0.5f, __fsub_rn(p2, p0), f);
+    B = -__fsub_rn(__fadd_rn(__fsub_rn(__fmul_rn(2.0f, p0), __fmul_rn(5.0f, p1)), __fmul_rn(4.0f, p2)), p3);
+    C = __fmul_rn(-1.5f, __fadd_rn(__fsub_rn(__fsub_rn(__fmul_rn(3.0f, p1), p0), __fmul_rn(3.0f, p2)), p3));
 }
 
 // Site index i modulo L for any int64 position (windows may wrap more than once on short chains).

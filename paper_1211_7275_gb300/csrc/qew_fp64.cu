@@ -3,16 +3,29 @@
 // HBM for the cell they were drawn for (regenerated when the site changes cell).
 //
 // Method: Eq. 1 of arXiv:1211.7275 with eta = c = 1, periodic in x, explicit Euler with all
-// forces from the old state (Sec. III.B); pinning force by linear interpolation of R (RF) or as
-// minus the derivative of the Catmull-Rom spline through V (RB) (Sec. III.B, Sec. IV.C);
-// observables of Eqs. 3-5.  Every FP64 operation is an explicit round-to-nearest intrinsic so
-// that no multiply-add is contracted: the rounding sequence is the textbook one, operation by
-// operation, (1 - d) R(n) + d R(n+1) for the force and u + dt ((lap + f) + F) for the update,
-// with lap = (u_{i+1} + u_{i-1}) - 2 u_i.
+// forces from the old state (Sec. III.B); pinning force by linear interpolation of R (RF), as
+// minus the derivative of the Catmull-Rom spline through V or G (cubic random bond, Cases 1-2),
+// or as G(n) - G(n+1) (linear-spline random bond, Case 3) (Sec. III.B, Sec. IV.C); observables
+// of Eqs. 3-5.  Every FP64 operation is an explicit round-to-nearest intrinsic so that no
+// multiply-add is contracted: the rounding sequence is the textbook one, operation by operation,
+// (1 - d) R(n) + d R(n+1) for the force and u + dt ((lap + f) + F) for the update, with
+// lap = (u_{i+1} + u_{i-1}) - 2 u_i.
 #include "qew_internal.h"
 
 namespace qew {
 namespace {
+
+// One disorder node in FP64: R (RF), V (uniform random bond) or G (Gaussian random bond).
+template <int KIND>
+__device__ __forceinline__ double node_f64(uint64_t seed, uint32_t s, int32_t i, int32_t n)
+{
+    if constexpr (KIND == kRF)
+        return rf_f64(seed, s, i, n);
+    else if constexpr (KIND == kRB)
+        return rb_f64(seed, s, i, n);
+    else
+        return rbg_f64(seed, s, i, n);
+}
 
 template <int KIND>
 __device__ __forceinline__ double pinning_f64(double u, int64_t p, int32_t i, uint32_t s, uint64_t seed,
@@ -25,7 +38,7 @@ __device__ __forceinline__ double pinning_f64(double u, int64_t p, int32_t i, ui
         const int32_t n = static_cast<int32_t>(fl);
         const double d = __dsub_rn(u, fl);
         const int32_t nc = st.ncache[p];
-        if constexpr (KIND == kRF) {
+        if constexpr (pair_kind(KIND)) {
             double r0, r1;
             if (n == nc) {
                 r0 = st.c[0][p];
@@ -33,19 +46,22 @@ __device__ __forceinline__ double pinning_f64(double u, int64_t p, int32_t i, ui
             } else {
                 if (n == nc + 1) {
                     r0 = st.c[1][p];
-                    r1 = rf_f64(seed, s, i, n + 1);
+                    r1 = node_f64<KIND>(seed, s, i, n + 1);
                 } else if (n == nc - 1) {
                     r1 = st.c[0][p];
-                    r0 = rf_f64(seed, s, i, n);
+                    r0 = node_f64<KIND>(seed, s, i, n);
                 } else {
-                    r0 = rf_f64(seed, s, i, n);
-                    r1 = rf_f64(seed, s, i, n + 1);
+                    r0 = node_f64<KIND>(seed, s, i, n);
+                    r1 = node_f64<KIND>(seed, s, i, n + 1);
                 }
                 st.ncache[p] = n;
                 st.c[0][p] = r0;
                 st.c[1][p] = r1;
             }
-            return __dadd_rn(__dmul_rn(__dsub_rn(1.0, d), r0), __dmul_rn(d, r1));
+            if constexpr (KIND == kRF)
+                return __dadd_rn(__dmul_rn(__dsub_rn(1.0, d), r0), __dmul_rn(d, r1));
+            else
+                return __dsub_rn(r0, r1);   // minus the slope of the linear spline through G
         } else {
             double p0, p1, p2, p3;
             if (n == nc) {
@@ -58,17 +74,17 @@ __device__ __forceinline__ double pinning_f64(double u, int64_t p, int32_t i, ui
                     p0 = st.c[1][p];
                     p1 = st.c[2][p];
                     p2 = st.c[3][p];
-                    p3 = rb_f64(seed, s, i, n + 2);
+                    p3 = node_f64<KIND>(seed, s, i, n + 2);
                 } else if (n == nc - 1) {
                     p1 = st.c[0][p];
                     p2 = st.c[1][p];
                     p3 = st.c[2][p];
-                    p0 = rb_f64(seed, s, i, n - 1);
+                    p0 = node_f64<KIND>(seed, s, i, n - 1);
                 } else {
-                    p0 = rb_f64(seed, s, i, n - 1);
-                    p1 = rb_f64(seed, s, i, n);
-                    p2 = rb_f64(seed, s, i, n + 1);
-                    p3 = rb_f64(seed, s, i, n + 2);
+                    p0 = node_f64<KIND>(seed, s, i, n - 1);
+                    p1 = node_f64<KIND>(seed, s, i, n);
+                    p2 = node_f64<KIND>(seed, s, i, n + 1);
+                    p3 = node_f64<KIND>(seed, s, i, n + 2);
                 }
                 st.ncache[p] = n;
                 st.c[0][p] = p0;
@@ -171,9 +187,15 @@ __global__ void f64_init_kernel(const ChainDesc* chains, const TileDesc* tiles, 
         if (ch.kind == kRF) {
             st.c[0][p] = rf_f64(seed, ch.s, i, n);
             st.c[1][p] = rf_f64(seed, ch.s, i, n + 1);
+        } else if (ch.kind == kRBGLinear) {
+            st.c[0][p] = rbg_f64(seed, ch.s, i, n);
+            st.c[1][p] = rbg_f64(seed, ch.s, i, n + 1);
         } else if (ch.kind == kRB) {
             for (int c = 0; c < 4; ++c)
                 st.c[c][p] = rb_f64(seed, ch.s, i, n - 1 + c);
+        } else if (ch.kind == kRBGCubic) {
+            for (int c = 0; c < 4; ++c)
+                st.c[c][p] = rbg_f64(seed, ch.s, i, n - 1 + c);
         }
     }
 }
@@ -200,6 +222,10 @@ __global__ void __launch_bounds__(256) f64_step_any(F64Launch a)
         f64_step_body<kRF>(a);
     else if (kind == kRB)
         f64_step_body<kRB>(a);
+    else if (kind == kRBGLinear)
+        f64_step_body<kRBGLinear>(a);
+    else if (kind == kRBGCubic)
+        f64_step_body<kRBGCubic>(a);
     else
         f64_step_body<kNone>(a);
 }
@@ -212,6 +238,10 @@ __global__ void __launch_bounds__(256) f64_observe_any(F64Launch a)
         f64_observe_body<kRF>(a, red);
     else if (kind == kRB)
         f64_observe_body<kRB>(a, red);
+    else if (kind == kRBGLinear)
+        f64_observe_body<kRBGLinear>(a, red);
+    else if (kind == kRBGCubic)
+        f64_observe_body<kRBGCubic>(a, red);
     else
         f64_observe_body<kNone>(a, red);
 }

@@ -87,13 +87,20 @@ __global__ void __launch_bounds__(kNaWarps * 32) na_tile_sums(const int32_t* __r
         const float d = __ldg(off + base + i);
         float g = f;
         if (kind == qew::kRF) {
-            const float q0 = qew::rf_f32(seed, static_cast<uint32_t>(c), i, n) + f;
-            const float q1 = qew::rf_f32(seed, static_cast<uint32_t>(c), i, n + 1) + f;
+            const float q0 = qew::rf_plus_f32(seed, static_cast<uint32_t>(c), i, n, f);
+            const float q1 = qew::rf_plus_f32(seed, static_cast<uint32_t>(c), i, n + 1, f);
             g = fmaf(d, q1 - q0, q0);
+        } else if (kind == qew::kRBGLinear) {
+            g = (qew::rbg_f32(seed, c, i, n) - qew::rbg_f32(seed, c, i, n + 1)) + f;
         } else if (kind == qew::kRB) {
             float A, B, C;
             qew::rb_coefficients(qew::rb_f32(seed, c, i, n - 1), qew::rb_f32(seed, c, i, n),
                                  qew::rb_f32(seed, c, i, n + 1), qew::rb_f32(seed, c, i, n + 2), f, A, B, C);
+            g = fmaf(d, fmaf(d, C, B), A);
+        } else if (kind == qew::kRBGCubic) {
+            float A, B, C;
+            qew::rb_coefficients(qew::rbg_f32(seed, c, i, n - 1), qew::rbg_f32(seed, c, i, n),
+                                 qew::rbg_f32(seed, c, i, n + 1), qew::rbg_f32(seed, c, i, n + 2), f, A, B, C);
             g = fmaf(d, fmaf(d, C, B), A);
         }
         sF += g - f;
@@ -163,7 +170,7 @@ extern "C" int qew_observe_state_noalloc(const int32_t* cell, const float* off, 
         return na_fail(QEW_EINVAL, "cell and off must be device pointers, not NULL");
     if (L < 1 || L >= (int64_t(1) << 31) || batch < 1)
         return na_fail(QEW_EINVAL, "need 1 <= L < 2^31 and batch >= 1");
-    if (disorder_kind < QEW_RF_GAUSS_LINEAR || disorder_kind > QEW_NONE)
+    if (disorder_kind < QEW_RF_GAUSS_LINEAR || disorder_kind > QEW_RB_GAUSS_CATMULLROM)
         return na_fail(QEW_EINVAL, "unknown disorder kind");
     const int64_t tiles_per_chain = (L + kNaTile - 1) / kNaTile;
     if (batch > kNaMaxChains || tiles_per_chain * batch > kNaMaxTiles)

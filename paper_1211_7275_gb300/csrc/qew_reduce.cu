@@ -69,8 +69,10 @@ __global__ void disorder_values_kernel(int kind, int fp64, uint64_t seed, uint32
         double v;
         if (kind == kRF)
             v = fp64 ? rf_f64(seed, s, ii, nn) : static_cast<double>(rf_f32(seed, s, ii, nn));
-        else
+        else if (kind == kRB)
             v = fp64 ? rb_f64(seed, s, ii, nn) : static_cast<double>(rb_f32(seed, s, ii, nn));
+        else
+            v = fp64 ? rbg_f64(seed, s, ii, nn) : static_cast<double>(rbg_f32(seed, s, ii, nn));
         out[k] = v;
     }
 }

@@ -8,8 +8,10 @@
 // Eqs. 3-5 (Sec. II).
 //
 // State of a site: integer cell n and FP32 offset d in [0, 1) (u = n + d), held in registers,
-// plus its disorder cache, held in shared memory: RF (R(n) + f, R(n+1) + f) -- the drive f is
-// folded in, so F_p + f is one subtraction and one FMA -- and RB V(n-1 .. n+2) with the cubic
+// plus its disorder cache, held in shared memory.  Pair kinds keep the two nodes of the cell:
+// RF (R(n) + f, R(n+1) + f) -- the drive f is folded in, so F_p + f is one subtraction and one
+// FMA -- and the linear-spline random bond (G(n), G(n+1)), F_p + f = (G(n) - G(n+1)) + f.  Quad
+// kinds (cubic random bond, uniform V or Gaussian G) keep V(n-1 .. n+2) with the cubic
 // coefficients of F_p + f beside them.
 //
 // Work decomposition: one warp owns one tile of 32 * S sites of a chain, S consecutive sites
@@ -55,9 +57,27 @@ __device__ __forceinline__ int32_t site_index(int64_t wstart, int x, bool contig
 // the 4-byte cell the cache was drawn for).
 template <int KIND>
 struct CacheBytes {
-    static constexpr int hbm = (KIND == kRF) ? 8 : (KIND == kRB) ? 16 : 0;
-    static constexpr int smem = (KIND == kRF) ? 12 : (KIND == kRB) ? 36 : 0;
+    static constexpr int hbm = pair_kind(KIND) ? 8 : quad_kind(KIND) ? 16 : 0;
+    static constexpr int smem = pair_kind(KIND) ? 12 : quad_kind(KIND) ? 36 : 0;
 };
+
+// F_p + f at window position x with offset d, from the shared-memory cache.
+template <int KIND>
+__device__ __forceinline__ float drive_plus_pinning(const float2* s_rf, const float4* s_co, int x, float d, float f)
+{
+    if constexpr (KIND == kRF) {
+        const float2 q = s_rf[x];
+        return fmaf(d, q.y - q.x, q.x);
+    } else if constexpr (KIND == kRBGLinear) {
+        const float2 q = s_rf[x];
+        return (q.x - q.y) + f;
+    } else if constexpr (quad_kind(KIND)) {
+        const float4 co = s_co[x];
+        return fmaf(d, fmaf(d, co.z, co.y), co.x);
+    } else {
+        return f;
+    }
+}
 
 // Queue entry codes (bits 16..17 of the first word; bits 0..15 hold the window position).
 constexpr int kMoveUp = 1;
@@ -68,10 +88,10 @@ constexpr int kMoveFar = 3;
 // the largest count for which the kernel still needs no (or almost no) register spills.
 template <int KIND, int S>
 struct MinBlocks {
-    static constexpr int value = (S <= 8) ? ((KIND == kRB) ? 3 : 4) : (S <= 16) ? ((KIND == kRB) ? 2 : 3) : 2;
+    static constexpr int value = (S <= 8) ? (quad_kind(KIND) ? 3 : 4) : (S <= 16) ? (quad_kind(KIND) ? 2 : 3) : 2;
 };
 
-// Sites per lane are odd: lane l reads its cache at word offsets 2 S l (RF) or 4 S l (RB), and
+// Sites per lane are odd: lane l reads its cache at word offsets 2 S l (pair) or 4 S l (quad), and
 // an odd S spreads a half-warp (quarter-warp for 16-byte loads) over distinct shared-memory banks.
 
 template <int KIND, int S>
@@ -92,9 +112,9 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     int32_t* s_cell = reinterpret_cast<int32_t*>(wsm);          // staging of n (load/store)
     float* s_off = reinterpret_cast<float*>(wsm + 4 * TW);      // staging of d (load/store)
     int2* s_queue = reinterpret_cast<int2*>(wsm);               // request queue (during the K loop)
-    float2* s_rf = reinterpret_cast<float2*>(wsm + 8 * TW);     // RF cache
-    float4* s_rb = reinterpret_cast<float4*>(wsm + 8 * TW);     // RB values V(n-1..n+2)
-    float4* s_co = reinterpret_cast<float4*>(wsm + 24 * TW);    // RB coefficients (A, B, C, -)
+    float2* s_rf = reinterpret_cast<float2*>(wsm + 8 * TW);     // pair cache (the cell's two nodes)
+    float4* s_rb = reinterpret_cast<float4*>(wsm + 8 * TW);     // quad values V(n-1..n+2)
+    float4* s_co = reinterpret_cast<float4*>(wsm + 24 * TW);    // quad coefficients (A, B, C, -)
     int32_t* s_ccell = reinterpret_cast<int32_t*>(wsm + (8 + CacheBytes<KIND>::smem - 4) * TW);  // cache's cell
 
     const TileDesc td = a.tiles[tile];
@@ -125,9 +145,9 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
             mbar_arrive_expect_tx(bar, TW * (8 + CacheBytes<KIND>::hbm));
             tma_load_1d(s_cell, a.in.cell + p0, TW * 4, bar);
             tma_load_1d(s_off, a.in.off + p0, TW * 4, bar);
-            if constexpr (KIND == kRF)
+            if constexpr (pair_kind(KIND))
                 tma_load_1d(s_rf, a.in.rf + p0, TW * 8, bar);
-            if constexpr (KIND == kRB)
+            if constexpr (quad_kind(KIND))
                 tma_load_1d(s_rb, a.in.rb + p0, TW * 16, bar);
         }
         const bool landed = __all_sync(kFull, mbar_wait(bar, 0));   // warp-uniform outcome
@@ -145,9 +165,9 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
             const int64_t p = ch.offset + site_index(wstart, x, contiguous, L);
             s_cell[x] = __ldg(g_cell + p);
             s_off[x] = __ldg(g_off + p);
-            if constexpr (KIND == kRF)
+            if constexpr (pair_kind(KIND))
                 s_rf[x] = __ldg(a.in.rf + p);
-            if constexpr (KIND == kRB)
+            if constexpr (quad_kind(KIND))
                 s_rb[x] = __ldg(a.in.rb + p);
         }
         __syncwarp();
@@ -166,7 +186,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
         d[j] = s_off[x];
         if constexpr (KIND != kNone)
             s_ccell[x] = s_cell[x];
-        if constexpr (KIND == kRB) {
+        if constexpr (quad_kind(KIND)) {
             const float4 p = s_rb[x];
             float A, B, C;
             rb_coefficients(p.x, p.y, p.z, p.w, f, A, B, C);
@@ -191,16 +211,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
             const float cn = (j + 1 < S) ? c[j + 1] : cr;
             const float dd = (j + 1 < S) ? d[j + 1] : drn;
             const float Dp = (cn - c[j]) + (dd - d[j]);   // u_{j+1} - u_j
-            float g;                                       // F_p + f
-            if constexpr (KIND == kRF) {
-                const float2 q = s_rf[x];
-                g = fmaf(d[j], q.y - q.x, q.x);
-            } else if constexpr (KIND == kRB) {
-                const float4 co = s_co[x];
-                g = fmaf(d[j], fmaf(d[j], co.z, co.y), co.x);
-            } else {
-                g = f;
-            }
+            const float g = drive_plus_pinning<KIND>(s_rf, s_co, x, d[j], f);   // F_p + f
             const float dn = fmaf(dt, (Dp - Dm) + g, d[j]);
             Dm = Dp;
             // Branch-free renormalisation.  d - floor(d) is exact; a tiny negative d can round up
@@ -245,9 +256,9 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                         s_ccell[x] = nn;
                         const int code = (nn == prev + 1) ? kMoveUp : (nn == prev - 1) ? kMoveDown : kMoveFar;
                         const int32_t i = site_index(wstart, x, contiguous, L);
-                        if constexpr (KIND == kRF) {
-                            // one new value: R(n+1) after an up move, R(n) otherwise
-                            const float v = rf_f32(a.keys, s, i, code == kMoveUp ? nn + 1 : nn) + f;
+                        if constexpr (pair_kind(KIND)) {
+                            // one new node: n+1 after an up move, n otherwise
+                            const float v = pair_node_f32<KIND>(a.keys, s, i, code == kMoveUp ? nn + 1 : nn, f);
                             const float2 o = s_rf[x];
                             float2 q;
                             if (code == kMoveUp)
@@ -255,11 +266,11 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                             else if (code == kMoveDown)
                                 q = make_float2(v, o.x);
                             else
-                                q = make_float2(v, rf_f32(a.keys, s, i, nn + 1) + f);
+                                q = make_float2(v, pair_node_f32<KIND>(a.keys, s, i, nn + 1, f));
                             s_rf[x] = q;
                         } else {
-                            // one new value: V(n+2) after an up move, V(n-1) otherwise
-                            const float v = rb_f32(a.keys, s, i, code == kMoveUp ? nn + 2 : nn - 1);
+                            // one new node: n+2 after an up move, n-1 otherwise
+                            const float v = quad_node_f32<KIND>(a.keys, s, i, code == kMoveUp ? nn + 2 : nn - 1);
                             const float4 o = s_rb[x];
                             float4 p;
                             if (code == kMoveUp)
@@ -267,8 +278,9 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                             else if (code == kMoveDown)
                                 p = make_float4(v, o.x, o.y, o.z);
                             else
-                                p = make_float4(v, rb_f32(a.keys, s, i, nn), rb_f32(a.keys, s, i, nn + 1),
-                                                rb_f32(a.keys, s, i, nn + 2));
+                                p = make_float4(v, quad_node_f32<KIND>(a.keys, s, i, nn),
+                                                quad_node_f32<KIND>(a.keys, s, i, nn + 1),
+                                                quad_node_f32<KIND>(a.keys, s, i, nn + 2));
                             s_rb[x] = p;
                             float A, B, C;
                             rb_coefficients(p.x, p.y, p.z, p.w, f, A, B, C);
@@ -299,15 +311,12 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
             const int x = lane * S + j;
             const int o = x - K;
             if (o >= 0 && o < owned) {
-                float g = f;
-                if constexpr (KIND == kRF) {
+                if constexpr (KIND == kRBGLinear) {
                     const float2 q = s_rf[x];
-                    g = fmaf(d[j], q.y - q.x, q.x);
-                } else if constexpr (KIND == kRB) {
-                    const float4 co = s_co[x];
-                    g = fmaf(d[j], fmaf(d[j], co.z, co.y), co.x);
+                    sF += q.x - q.y;
+                } else {
+                    sF += drive_plus_pinning<KIND>(s_rf, s_co, x, d[j], f) - f;
                 }
-                sF += g - f;
                 const float y = c[j] + d[j];   // u - N0
                 sy += y;
                 syy = fmaf(y, y, syy);
@@ -351,9 +360,9 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
             const uint32_t cnt = static_cast<uint32_t>(owned);
             tma_store_1d(a.out.cell + out0, s_cell + K, cnt * 4);
             tma_store_1d(a.out.off + out0, s_off + K, cnt * 4);
-            if constexpr (KIND == kRF)
+            if constexpr (pair_kind(KIND))
                 tma_store_1d(a.out.rf + out0, s_rf + K, cnt * 8);
-            if constexpr (KIND == kRB)
+            if constexpr (quad_kind(KIND))
                 tma_store_1d(a.out.rb + out0, s_rb + K, cnt * 16);
             tma_store_commit();
             tma_store_wait_all();
@@ -365,9 +374,9 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
             const int64_t p = out0 + o;
             a.out.cell[p] = s_cell[x];
             a.out.off[p] = s_off[x];
-            if constexpr (KIND == kRF)
+            if constexpr (pair_kind(KIND))
                 a.out.rf[p] = s_rf[x];
-            if constexpr (KIND == kRB)
+            if constexpr (quad_kind(KIND))
                 a.out.rb[p] = s_rb[x];
         }
     }
@@ -424,10 +433,15 @@ __global__ void split_init_kernel(const ChainDesc* chains, const TileDesc* tiles
         st.cell[p] = n;
         st.off[p] = d;
         if (ch.kind == kRF)
-            st.rf[p] = make_float2(rf_f32(seed, ch.s, i, n) + ch.f32, rf_f32(seed, ch.s, i, n + 1) + ch.f32);
+            st.rf[p] = make_float2(rf_plus_f32(seed, ch.s, i, n, ch.f32), rf_plus_f32(seed, ch.s, i, n + 1, ch.f32));
+        else if (ch.kind == kRBGLinear)
+            st.rf[p] = make_float2(rbg_f32(seed, ch.s, i, n), rbg_f32(seed, ch.s, i, n + 1));
         else if (ch.kind == kRB)
             st.rb[p] = make_float4(rb_f32(seed, ch.s, i, n - 1), rb_f32(seed, ch.s, i, n), rb_f32(seed, ch.s, i, n + 1),
                                    rb_f32(seed, ch.s, i, n + 2));
+        else if (ch.kind == kRBGCubic)
+            st.rb[p] = make_float4(rbg_f32(seed, ch.s, i, n - 1), rbg_f32(seed, ch.s, i, n),
+                                   rbg_f32(seed, ch.s, i, n + 1), rbg_f32(seed, ch.s, i, n + 2));
     }
 }
 
@@ -452,14 +466,14 @@ __global__ void split_to_f64_kernel(const ChainDesc* chains, const TileDesc* til
 
 bool split_supported(int kind, int S)
 {
-    if (kind == kRB)
+    if (quad_kind(kind))
         return S == 7 || S == 15;
     return S == 7 || S == 15 || S == 23 || S == 31;
 }
 
 size_t split_smem_bytes(int kind, int S, int tiles_per_cta)
 {
-    const int cache = (kind == kRF) ? 12 : (kind == kRB) ? 36 : 0;
+    const int cache = pair_kind(kind) ? 12 : quad_kind(kind) ? 36 : 0;
     return static_cast<size_t>(tiles_per_cta) * 32 * S * (8 + cache);
 }
 
@@ -472,12 +486,24 @@ cudaError_t split_step(int kind, int S, int tiles_per_cta, const SplitLaunch& a,
         case 23: return launch_split<kRF, 23>(tiles_per_cta, a, st);
         case 31: return launch_split<kRF, 31>(tiles_per_cta, a, st);
         }
+    } else if (kind == kRBGLinear) {
+        switch (S) {
+        case 7: return launch_split<kRBGLinear, 7>(tiles_per_cta, a, st);
+        case 15: return launch_split<kRBGLinear, 15>(tiles_per_cta, a, st);
+        case 23: return launch_split<kRBGLinear, 23>(tiles_per_cta, a, st);
+        case 31: return launch_split<kRBGLinear, 31>(tiles_per_cta, a, st);
+        }
     } else if (kind == kRB) {
         switch (S) {
         case 7: return launch_split<kRB, 7>(tiles_per_cta, a, st);
         case 15: return launch_split<kRB, 15>(tiles_per_cta, a, st);
         }
-    } else {
+    } else if (kind == kRBGCubic) {
+        switch (S) {
+        case 7: return launch_split<kRBGCubic, 7>(tiles_per_cta, a, st);
+        case 15: return launch_split<kRBGCubic, 15>(tiles_per_cta, a, st);
+        }
+    } else if (kind == kNone) {
         switch (S) {
         case 7: return launch_split<kNone, 7>(tiles_per_cta, a, st);
         case 15: return launch_split<kNone, 15>(tiles_per_cta, a, st);

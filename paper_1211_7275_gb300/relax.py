@@ -11,7 +11,7 @@ import ctypes
 import numpy as np
 
 from . import _capi
-from ._capi import FP32_SPLIT, FP64, NONE, RB_UNIFORM_CATMULLROM, RF_GAUSS_LINEAR  # noqa: F401
+from ._capi import FP32_SPLIT, FP64, NONE, RB_GAUSS_CATMULLROM, RB_GAUSS_LINEAR, RB_UNIFORM_CATMULLROM, RF_GAUSS_LINEAR  # noqa: F401
 
 
 def _ptr(a: np.ndarray):

@@ -1,13 +1,14 @@
 """Write ``fc_<kind>_L4096.json``: the finite-size critical force at L = 4096 of the random-field
 chain (R ~ N(0,1), linear interpolation; ``rf``) or of the Gaussian random-bond chain with a
-linear spline (Case 3 of Sec. IV.C; ``rbg_linear``), found by bisection with the CPU oracle only.
+linear spline (Case 3 of Sec. IV.C; ``rbg_linear``) or a Catmull-Rom spline (Case 1;
+``rbg_cubic``), found by bisection with the CPU oracle only.
 
 Criterion (the short-time-dynamics bracketing of Sec. III.A, made concrete): relax 8 samples
 from the flat start to t = 500 and fit the log-log slope of V(t) t^{beta/nu z} over the last
 decade of t, with beta/nu z = 0.128 (Sec. IV.E).  A positive slope means V saturates (f above
 f_c), a negative one that V decays faster than the critical power law (f below f_c).
 
-Run: python tests/golden/make_fc_oracle.py rf|rbg_linear   (about a minute each on 8 cores)
+Run: python tests/golden/make_fc_oracle.py rf|rbg_linear|rbg_cubic   (about a minute each on 8 cores)
 """
 import json
 import os
@@ -22,7 +23,8 @@ import oracle  # noqa: E402
 from qew_workloads import SEED, log_spaced_steps  # noqa: E402
 
 L, N_SAMPLES, DT, N_STEPS, BETA_NU_Z = 4096, 8, 0.1, 5000, 0.128
-KINDS = {"rf": ("RF", oracle.KIND_RF), "rbg_linear": ("RB Gaussian, linear spline", oracle.KIND_RBG_LINEAR)}
+KINDS = {"rf": ("RF", oracle.KIND_RF), "rbg_linear": ("RB Gaussian, linear spline", oracle.KIND_RBG_LINEAR),
+         "rbg_cubic": ("RB Gaussian, Catmull-Rom spline", oracle.KIND_RBG_CUBIC)}
 
 
 def drift(f: float, kind: int) -> float:

@@ -13,6 +13,8 @@ Case 3 (Gaussian random-bond potential, linear spline; Sec. IV.C) gets the same 
 its own oracle-bisected f_c^L (``tests/golden/fc_rbg_linear_L4096.json``), plus one more pin:
 with N(0,1) potential values its f_c^L lands on Table I's Case 3 value, 1.565 at L = 4096, so
 the amplitude, the spline and the sign of the force are checked against a printed number.
+Case 1 (Gaussian potential, cubic spline) is compared with Table I more loosely, since its
+spline here is the local Catmull-Rom one.
 """
 import json
 import os
@@ -78,7 +80,7 @@ def test_transition_brackets(runs):
     assert abs(_slope(t, out["above"][0], 50, 500)) < 0.05
 
 
-@pytest.mark.parametrize("name", ["rf", "rbg_linear"])
+@pytest.mark.parametrize("name", ["rf", "rbg_linear", "rbg_cubic"])
 def test_fc_fixture_provenance(name):
     fc = _load(f"fc_{name}_L4096.json")
     assert fc["_made_by"].startswith(f"tests/golden/make_fc_oracle.py {name}")
@@ -92,6 +94,15 @@ def test_case3_fc_matches_table1():
     # Table I quotes 1.565 +- 0.002; the bisection here uses 8 samples and a shorter time
     # window, so allow 1% (a wrong amplitude, spline or sign moves it by tens of percent)
     assert abs(fc["f_c"] - paper["case3_rb_gauss_linear_L4096"]) < 0.01 * paper["case3_rb_gauss_linear_L4096"]
+
+
+def test_case1_fc_near_table1():
+    """Case 1 here interpolates with the local Catmull-Rom cubic, not the paper's cubic spline over
+    the whole periodic column (only the microscopic correlator differs, Sec. III.B), so its f_c^L
+    is compared loosely: within 5% of Table I's 1.915."""
+    paper = _load("paper_values.json")["critical_forces"]
+    fc = _load("fc_rbg_cubic_L4096.json")
+    assert abs(fc["f_c"] - paper["case1_rb_gauss_cubic_L4096"]) < 0.05 * paper["case1_rb_gauss_cubic_L4096"]
 
 
 def test_case3_exponents_at_fc(runs_case3):
