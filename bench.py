@@ -36,11 +36,14 @@ import qew_workloads as W  # noqa: E402
 METRIC = "site-updates/s and % binding roofline, qEW Euler at L=2^25, FP32-split vs FP64, 1 GB300"
 UNIT = "site-updates/s"
 
-# Algorithmic lane operations per site-update of the fused kernel (derivation in the design doc):
-# elastic force 5, pinning 2 (RF) / 2 (RB) / 0 (none), Euler 2, cell test 1; plus, per cell
-# crossing, one Philox4x32-10 block (10 rounds x 6) and the value transform.
-OPS_BASE = {0: 10, 1: 10, 2: 8}
-OPS_PER_CROSSING = {0: 90, 1: 62, 2: 0}
+# Algorithmic lane operations per site-update of the fused kernel, per disorder kind (0 RF,
+# 1 uniform RB cubic, 2 none, 3 Gaussian RB linear, 4 Gaussian RB cubic): elastic force 6,
+# pinning 2 (linear) / 8 (cubic) / 0 (none), Euler 3, renormalisation and cell test 3; plus, per
+# cell crossing, one Philox4x32-10 block (~90 integer operations with its key schedule) and the
+# value transform (Box-Muller ~13, uniform ~2).  Derivation in the design doc.
+OPS_BASE = {0: 14, 1: 20, 2: 12, 3: 14, 4: 20}
+OPS_PER_CROSSING = {0: 103, 1: 92, 2: 0, 3: 103, 4: 103}
+QUAD_KINDS = (1, 4)
 LANES_PER_SM = 128
 
 
@@ -327,7 +330,7 @@ def main() -> None:
     achieved = ops_per_su * su_per_launch / (per_launch_ms / 1e3) / 1e12
     peak = sms * LANES_PER_SM * clk * 1e6 / 1e12
     tile_w, K, tpc = tuning
-    bytes_per_su = 2 * (8 + 4 * (2 if kind != 1 else 4)) / K      # state + cache, read + write per K steps
+    bytes_per_su = 2 * (8 + 4 * (4 if kind in QUAD_KINDS else 2 if kind != 2 else 0)) / K   # state + cache, r+w per K steps
     hbm_achieved = bytes_per_su * su_per_launch / (per_launch_ms / 1e3) / 1e9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     traffic = profiled_traffic()

@@ -23,12 +23,13 @@
 // shuffles per neighbour and there is no block-wide barrier.
 //
 // Cell crossings: renormalisation is branch-free (n += floor(d), d -= floor(d)) and leaves one
-// bit per moved site; after the update loop a warp prefix sum of the lanes' move counts places
-// one request per moved site into the warp's queue in shared memory (no atomics, deterministic
-// order).
-// The queued Philox values are then evaluated 32 lanes at a time and written straight into the
-// shared-memory cache of the requesting sites; the direction of each move is recovered from the
-// cell the cache was drawn for, kept per site in shared memory.
+// bit per moved site.  After the update loop each lane stores its cells to shared memory (16-byte
+// stores; a store inside the update loop would keep the compiler from hoisting the cache loads
+// there), and a warp prefix sum of the lanes' move counts gives each
+// lane its queue slots, which it fills by walking the set bits of its mask (no atomics,
+// deterministic order).  The queued Philox values are then evaluated 32 lanes at a time and
+// written straight into the shared-memory cache of the requesting sites; the direction of each
+// move is recovered from the cell the cache was drawn for, kept per site in shared memory.
 #include <cstdio>
 
 #include "qew_internal.h"
@@ -111,7 +112,13 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     unsigned char* wsm = smem_raw + static_cast<size_t>(warp) * WARP_SMEM;
     int32_t* s_cell = reinterpret_cast<int32_t*>(wsm);          // staging of n (load/store)
     float* s_off = reinterpret_cast<float*>(wsm + 4 * TW);      // staging of d (load/store)
-    int2* s_queue = reinterpret_cast<int2*>(wsm);               // request queue (during the K loop)
+    // During the K loop the staging area holds each lane's cells after the step, one padded row
+    // of NEWC_ROW floats per lane (written with 16-byte stores), then a 32-entry request chunk.
+    constexpr int NEWC_ROW = ((S + 3) / 4 * 4) % 8 == 0 ? (S + 3) / 4 * 4 + 4 : (S + 3) / 4 * 4;
+    static_assert(NEWC_ROW % 8 == 4, "row stride of 4 mod 8 words: a quarter-warp of 16-byte stores hits distinct banks");
+    static_assert(32 * NEWC_ROW * 4 + 32 * 4 <= 8 * TW, "cell rows and request chunk fit in the staging area");
+    float* s_newc = reinterpret_cast<float*>(wsm);                          // [32][NEWC_ROW]
+    int* s_q = reinterpret_cast<int*>(wsm + 32 * NEWC_ROW * 4);             // request chunk
     float2* s_rf = reinterpret_cast<float2*>(wsm + 8 * TW);     // pair cache (the cell's two nodes)
     float4* s_rb = reinterpret_cast<float4*>(wsm + 8 * TW);     // quad values V(n-1..n+2)
     float4* s_co = reinterpret_cast<float4*>(wsm + 24 * TW);    // quad coefficients (A, B, C, -)
@@ -223,9 +230,16 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
         }
         const unsigned anymv = __reduce_or_sync(kFull, mv);
         if (anymv) {
-            // queue positions: warp prefix sum of the lanes' move counts, then each lane's moved
-            // sites in slot order (one predicated store per slot, no ballots or atomics); queue
-            // entry = (window position, new cell)
+            // the lane's cells after the step, read by the consumers below for the moved sites
+            if constexpr (KIND != kNone) {
+                float4* row = reinterpret_cast<float4*>(s_newc + lane * NEWC_ROW);
+#pragma unroll
+                for (int v = 0; v < (S + 3) / 4; ++v)
+                    row[v] = make_float4(c[4 * v], (4 * v + 1 < S) ? c[4 * v + 1] : 0.0f,
+                                         (4 * v + 2 < S) ? c[4 * v + 2] : 0.0f, (4 * v + 3 < S) ? c[4 * v + 3] : 0.0f);
+            }
+            // queue slots: warp prefix sum of the lanes' move counts; each lane then walks the set
+            // bits of its mask.  Chunks of 32 requests, one Philox value per lane and chunk.
             const int cnt = __popc(mv);
             int incl = cnt;
 #pragma unroll
@@ -235,23 +249,24 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                     incl += y;
             }
             const int qn = __shfl_sync(kFull, incl, 31);
-            const int qbase = incl - cnt;
-            if constexpr (KIND != kNone) {
-#pragma unroll
-                for (int j = 0; j < S; ++j) {
-                    if ((mv >> j) & 1u)
-                        s_queue[qbase + __popc(mv & ((1u << j) - 1u))] =
-                            make_int2(lane * S + j, N0 + __float2int_rn(c[j]));
-                }
-            }
             n_cross += (lane == 0) ? static_cast<unsigned>(qn) : 0u;
             if constexpr (KIND != kNone) {
-                __syncwarp();
+                const int excl = incl - cnt;
                 for (int base = 0; base < qn; base += 32) {
+                    int q = excl;
+                    unsigned m = mv;
+                    while (m != 0u && q < base + 32) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1u;
+                        if (q >= base)
+                            s_q[q - base] = (lane << 8) | b;
+                        ++q;
+                    }
+                    __syncwarp();
                     if (base + lane < qn) {
-                        const int2 e = s_queue[base + lane];
-                        const int x = e.x;
-                        const int nn = e.y;
+                        const int e = s_q[lane];
+                        const int x = (e >> 8) * S + (e & 0xff);
+                        const int nn = N0 + __float2int_rn(s_newc[(e >> 8) * NEWC_ROW + (e & 0xff)]);
                         const int prev = s_ccell[x];
                         s_ccell[x] = nn;
                         const int code = (nn == prev + 1) ? kMoveUp : (nn == prev - 1) ? kMoveDown : kMoveFar;
@@ -287,8 +302,8 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                             s_co[x] = make_float4(A, B, C, 0.0f);
                         }
                     }
+                    __syncwarp();
                 }
-                __syncwarp();
             }
         }
     }
