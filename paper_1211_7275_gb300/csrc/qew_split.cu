@@ -206,10 +206,17 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     unsigned n_cross = 0;
 #pragma unroll 1
     for (int k = 0; k < K; ++k) {
-        const float cl = __shfl_up_sync(kFull, c[S - 1], 1);
-        const float dl = __shfl_up_sync(kFull, d[S - 1], 1);
-        const float cr = __shfl_down_sync(kFull, c[0], 1);
-        const float drn = __shfl_down_sync(kFull, d[0], 1);
+        // Window positions 0 and TW - 1 take themselves as their outer neighbour: they go stale
+        // either way, and a zero slope there keeps the stale edge from drifting off and making
+        // spurious cell moves (each of which would draw disorder values).
+        const float cl0 = __shfl_up_sync(kFull, c[S - 1], 1);
+        const float dl0 = __shfl_up_sync(kFull, d[S - 1], 1);
+        const float cr0 = __shfl_down_sync(kFull, c[0], 1);
+        const float dr0 = __shfl_down_sync(kFull, d[0], 1);
+        const float cl = (lane == 0) ? c[0] : cl0;
+        const float dl = (lane == 0) ? d[0] : dl0;
+        const float cr = (lane == 31) ? c[S - 1] : cr0;
+        const float drn = (lane == 31) ? d[S - 1] : dr0;
         float Dm = (c[0] - cl) + (d[0] - dl);   // u_j - u_{j-1}
         unsigned mv = 0;   // sites that changed cell in this step
 #pragma unroll
