@@ -54,13 +54,16 @@ __device__ __forceinline__ int32_t site_index(int64_t wstart, int x, bool contig
     return wrap_site(g, L);
 }
 
-// Bytes of disorder cache per site in HBM / in shared memory (the shared-memory figure includes
-// the 4-byte cell the cache was drawn for).
+// Bytes of disorder cache per site in HBM / in shared memory (the shared-memory figure adds the
+// cubic coefficients; the cell each cache was drawn for stays in the staging area).
 template <int KIND>
 struct CacheBytes {
     static constexpr int hbm = pair_kind(KIND) ? 8 : quad_kind(KIND) ? 16 : 0;
-    static constexpr int smem = pair_kind(KIND) ? 12 : quad_kind(KIND) ? 36 : 0;
+    static constexpr int smem = pair_kind(KIND) ? 8 : quad_kind(KIND) ? 32 : 0;
 };
+
+// Per warp after its sites: one chunk of 32 queued moves.
+constexpr int kQueueBytes = 32 * 4;
 
 // F_p + f at window position x with offset d, from the shared-memory cache.
 template <int KIND>
@@ -99,7 +102,7 @@ template <int KIND, int S>
 __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_kernel(SplitLaunch a)
 {
     constexpr int TW = 32 * S;
-    constexpr int WARP_SMEM = TW * (8 + CacheBytes<KIND>::smem);
+    constexpr int WARP_SMEM = TW * (8 + CacheBytes<KIND>::smem) + kQueueBytes;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t s_bar[8];
 
@@ -112,17 +115,14 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     unsigned char* wsm = smem_raw + static_cast<size_t>(warp) * WARP_SMEM;
     int32_t* s_cell = reinterpret_cast<int32_t*>(wsm);          // staging of n (load/store)
     float* s_off = reinterpret_cast<float*>(wsm + 4 * TW);      // staging of d (load/store)
-    // During the K loop the staging area holds each lane's cells after the step, one padded row
-    // of NEWC_ROW floats per lane (written with 16-byte stores), then a 32-entry request chunk.
-    constexpr int NEWC_ROW = ((S + 3) / 4 * 4) % 8 == 0 ? (S + 3) / 4 * 4 + 4 : (S + 3) / 4 * 4;
-    static_assert(NEWC_ROW % 8 == 4, "row stride of 4 mod 8 words: a quarter-warp of 16-byte stores hits distinct banks");
-    static_assert(32 * NEWC_ROW * 4 + 32 * 4 <= 8 * TW, "cell rows and request chunk fit in the staging area");
-    float* s_newc = reinterpret_cast<float*>(wsm);                          // [32][NEWC_ROW]
-    int* s_q = reinterpret_cast<int*>(wsm + 32 * NEWC_ROW * 4);             // request chunk
+    // During the K loop the staged cells are the cells the caches were drawn for, and the staged
+    // offsets' slot of each site takes its cell after the step (relative to N0, as a float).
+    int32_t* s_ccell = s_cell;
+    float* s_newc = s_off;
+    int* s_q = reinterpret_cast<int*>(wsm + TW * (8 + CacheBytes<KIND>::smem));   // request chunk
     float2* s_rf = reinterpret_cast<float2*>(wsm + 8 * TW);     // pair cache (the cell's two nodes)
     float4* s_rb = reinterpret_cast<float4*>(wsm + 8 * TW);     // quad values V(n-1..n+2)
     float4* s_co = reinterpret_cast<float4*>(wsm + 24 * TW);    // quad coefficients (A, B, C, -)
-    int32_t* s_ccell = reinterpret_cast<int32_t*>(wsm + (8 + CacheBytes<KIND>::smem - 4) * TW);  // cache's cell
 
     const TileDesc td = a.tiles[tile];
     const ChainDesc ch = a.chains[td.chain];
@@ -191,8 +191,6 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
         const int x = lane * S + j;
         c[j] = static_cast<float>(s_cell[x] - N0);
         d[j] = s_off[x];
-        if constexpr (KIND != kNone)
-            s_ccell[x] = s_cell[x];
         if constexpr (quad_kind(KIND)) {
             const float4 p = s_rb[x];
             float A, B, C;
@@ -239,11 +237,9 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
         if (anymv) {
             // the lane's cells after the step, read by the consumers below for the moved sites
             if constexpr (KIND != kNone) {
-                float4* row = reinterpret_cast<float4*>(s_newc + lane * NEWC_ROW);
 #pragma unroll
-                for (int v = 0; v < (S + 3) / 4; ++v)
-                    row[v] = make_float4(c[4 * v], (4 * v + 1 < S) ? c[4 * v + 1] : 0.0f,
-                                         (4 * v + 2 < S) ? c[4 * v + 2] : 0.0f, (4 * v + 3 < S) ? c[4 * v + 3] : 0.0f);
+                for (int j = 0; j < S; ++j)
+                    s_newc[lane * S + j] = c[j];
             }
             // queue slots: warp prefix sum of the lanes' move counts; each lane then walks the set
             // bits of its mask.  Chunks of 32 requests, one Philox value per lane and chunk.
@@ -273,7 +269,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                     if (base + lane < qn) {
                         const int e = s_q[lane];
                         const int x = (e >> 8) * S + (e & 0xff);
-                        const int nn = N0 + __float2int_rn(s_newc[(e >> 8) * NEWC_ROW + (e & 0xff)]);
+                        const int nn = N0 + __float2int_rn(s_newc[x]);
                         const int prev = s_ccell[x];
                         s_ccell[x] = nn;
                         const int code = (nn == prev + 1) ? kMoveUp : (nn == prev - 1) ? kMoveDown : kMoveFar;
@@ -407,7 +403,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
 template <int KIND, int S>
 cudaError_t launch_split(int tiles_per_cta, const SplitLaunch& a, cudaStream_t st)
 {
-    const size_t smem = static_cast<size_t>(tiles_per_cta) * 32 * S * (8 + CacheBytes<KIND>::smem);
+    const size_t smem = static_cast<size_t>(tiles_per_cta) * (32 * S * (8 + CacheBytes<KIND>::smem) + kQueueBytes);
     auto kern = split_step_kernel<KIND, S>;
     // raise the dynamic shared-memory limit once per kernel and device to the largest shape in use
     static int s_limit[64] = {};
@@ -495,8 +491,8 @@ bool split_supported(int kind, int S)
 
 size_t split_smem_bytes(int kind, int S, int tiles_per_cta)
 {
-    const int cache = pair_kind(kind) ? 12 : quad_kind(kind) ? 36 : 0;
-    return static_cast<size_t>(tiles_per_cta) * 32 * S * (8 + cache);
+    const int cache = pair_kind(kind) ? 8 : quad_kind(kind) ? 32 : 0;
+    return static_cast<size_t>(tiles_per_cta) * (32 * S * (8 + cache) + kQueueBytes);
 }
 
 cudaError_t split_step(int kind, int S, int tiles_per_cta, const SplitLaunch& a, cudaStream_t st)
