@@ -40,7 +40,7 @@ UNIT = "site-updates/s"
 # 1 uniform RB cubic, 2 none, 3 Gaussian RB linear, 4 Gaussian RB cubic): elastic force 6,
 # pinning 2 (linear) / 8 (cubic) / 0 (none), Euler 3, renormalisation and cell test 3; plus, per
 # cell crossing, one Philox4x32-10 block (~90 integer operations with its key schedule) and the
-# value transform (Box-Muller ~13, uniform ~2).  Derivation in the design doc.
+# value transform (Box-Muller ~13, uniform ~2).
 OPS_BASE = {0: 14, 1: 20, 2: 12, 3: 14, 4: 20}
 OPS_PER_CROSSING = {0: 103, 1: 92, 2: 0, 3: 103, 4: 103}
 QUAD_KINDS = (1, 4)
@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="rf_4x2^25", choices=["rf_4x2^25", "rf_16x2^20", "rb_1024x2^16",
+                                                                "rbg_linear_4x2^25", "none_16x2^20",
                                                                 "tiny_rf_1x1024"])
     p.add_argument("--relax-steps", type=int, default=4096)
     p.add_argument("--n-obs", type=int, default=12)
@@ -229,7 +230,7 @@ def run_reference(args, rank: int, world: int) -> None:
     if rank != 0:
         return
     wl = workload(args.workload, 0)
-    w, n = 1 << 19, 8
+    w, n = 1 << 20, 48
     for _ in range(args.warmup):
         oracle_sample(wl, w, n)
     vals, secs = [], []
@@ -398,7 +399,7 @@ def main() -> None:
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(wl, 1 << 20, 24)
+        cpu = oracle_sample(wl, 1 << 20, 128)
         cpu.pop("seconds", None)
 
     if rank == 0:

@@ -214,3 +214,27 @@ def test_ensemble_at_fc_within_two_sigma(qew, orc, name, kind):
         print(f"{name} {key}: paired |FP32 - oracle| / sample sd, max over t: "
               f"{np.max(paired[1:] / np.maximum(ref[key].std(1, ddof=1)[1:], 1e-12)):.2e}")
         np.testing.assert_allclose(obs64[key][early], ref[key][early], rtol=1e-9, atol=1e-11)
+
+
+def test_full_size_case3_4x2e25(qew, orc):
+    """The Case 3 preset at full size (4 x 2^25 sites, f = 1.5652, the paper's L = 2^25 value for
+    this case) in the launch shape the autotuner picks: sampled sites (chain ends, tile edges,
+    random sites) after 100 steps against the oracle's light-cone evaluation of the same site, and
+    dubar = dt v on every chain."""
+    from qew_workloads import PRESETS, preset_f
+    p = PRESETS["rbg_linear_4x2^25"]
+    L, batch, n = p["L"], p["batch"], 100
+    f = preset_f("rbg_linear_4x2^25")
+    with qew.Relaxation(L, f, RBG_LINEAR, dt=0.1, seed=SEED, precision=FP32, batch=batch) as r:
+        r.set_tuning(0, 0, 0)
+        obs = r.observe(np.array([0, n - 1, n]))
+        u, _ = r.state()
+        tile_w, K, _ = r.tuning()
+    w_own = tile_w - 2 * K
+    rng = np.random.default_rng(5)
+    for c in range(batch):
+        for i in [0, 1, L - 1, w_own - 1, w_own, 7 * w_own + 3] + [int(x) for x in rng.integers(0, L, 3)]:
+            ref_u, _ = orc.lightcone(L, c, f, 0.1, RBG_LINEAR, SEED, i, 1, n)
+            assert abs(u[c * L + i] - ref_u[0]) <= 1e-4, (c, i, u[c * L + i], ref_u[0])
+    dub = obs["ubar"][2] - obs["ubar"][1]
+    assert np.all(np.abs(dub - 0.1 * obs["v"][1]) <= 2e-6 * np.maximum(1, np.abs(obs["ubar"][1])))

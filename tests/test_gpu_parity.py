@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
 
-Bars (BASELINE north star; Sec. II-III of arXiv:1211.7275 define what is computed):
+Bars (Sec. II-III of arXiv:1211.7275 define what is computed):
   - RNG words and integer cell indices: bit-exact (cells compared where the oracle's u is more
     than 1e-4 from an integer, where FP32 rounding cannot move the floor);
   - FP64 path: per site |du| <= 1e-12 max(1, |u|) over 10^3 steps;
