@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
 leg of ``bench.py`` may import this package.  The product library never loads it, and it
 shares no code with the CUDA path: the arithmetic lives in ``qew_oracle.c`` (plain C, FP64,
-no fused multiply-add), this module only marshals numpy arrays through ctypes.
+no fused multiply-add) and this module marshals numpy arrays through ctypes, except for the
+structure factor, which is numpy's FFT and a mean of squared moduli.
 
 Functions and the passages they follow:
   philox4x32_10      Philox4x32-10 block function (Salmon et al., SC'11); the paper does not
@@ -19,6 +20,8 @@ Functions and the passages they follow:
                      the flat start (Sec. II) or a given state, with v, ubar, w2 of Eqs. 3-5.
   lightcone          the same dynamics evaluated on a window of 2n+w sites, exact for the
                      w central sites after n steps (stencil radius 1).
+  structure_factor   S_q of Eq. 6 (Sec. II): the sample mean of |(1/L) sum_x u(x) e^{-iqx}|^2
+                     at q = 2 pi n / L, n = 1 .. L/2, by a real FFT of each chain.
 
 Parity of every function is pinned by ``tests/test_oracle_*.py``.
 """
@@ -173,3 +176,15 @@ def lightcone(L: int, s: int, f: float, dt: float, kind: int, seed: int, i0: int
     if rc != 0:
         raise ValueError(f"oracle_lightcone failed with status {rc}")
     return u, F
+
+
+def structure_factor(u, L: int, n_modes: int | None = None) -> np.ndarray:
+    """S_q of Eq. 6 for the chains of length ``L`` concatenated in ``u``: the mean over chains of
+    |(1/L) sum_x u(x) e^{-iqx}|^2 at q = 2 pi n / L for n = 1 .. n_modes (default L // 2).  Modes
+    n and L - n are equal for a real line, so n = 1 .. L/2 carry all of it."""
+    u = np.asarray(u, dtype=np.float64).reshape(-1, L)
+    m = L // 2 if n_modes is None else int(n_modes)
+    if not 1 <= m <= L // 2:
+        raise ValueError("n_modes must lie in [1, L/2]")
+    z = np.fft.rfft(u, axis=1)[:, 1:m + 1] / L
+    return np.mean(z.real ** 2 + z.imag ** 2, axis=0)
