@@ -346,6 +346,16 @@ def main() -> None:
                         "peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured)"},
                 "fused_share_of_step": st["fused_ms"] / ms if ms > 0 else None}
 
+    # ---- structure factor (Eq. 6) of the relaxed chains: one call, outside the timed region ----
+    sq = None
+    if len(set(np.atleast_1d(wl["L"]).tolist())) == 1:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = relax.structure_factor()
+        sq = {"ms": 1e3 * (time.perf_counter() - t0), "modes": int(S.size), "chains": int(wl["batch"]),
+              "includes": "state to FP64 rows, batched real-to-complex cuFFT, mean |u_q|^2 over chains, "
+                          "copy to host (work area allocated and freed in the call)"}
+
     # ---- FP64 plain path on the same chains (the comparison the metric names) ----
     fp64 = None
     if args.fp64_steps > 0:
@@ -413,7 +423,7 @@ def main() -> None:
                        "tuning": {"tile_w": tile_w, "K": K, "tiles_per_cta": tpc},
                        "l2": "inputs larger than L2 (4 GiB state), no flush",
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
-            "roofline": roofline, "fp64_path": fp64, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "fp64_path": fp64, "cpu_baseline": cpu, "e2e": e2e, "structure_factor": sq,
             "gpu_launches": st["launches"], "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

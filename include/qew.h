@@ -158,6 +158,19 @@ int qew_get_cells(qew_handle h, int32_t* cells_out);
  */
 int qew_set_state(qew_handle h, const double* u_in);
 
+/*
+ * qew_structure_factor -- the disorder-averaged structure factor of the current state (Eq. 6,
+ * Sec. II):  S_out[k] = (1/n_chains) sum_c |(1/L) sum_x u_c(x) e^{-iqx}|^2  at q = 2 pi (k+1) / L,
+ * for k < n_modes.  Modes n and L - n are equal for a real line, so 1 <= n_modes <= L/2 covers
+ * the spectrum.  All chains of the handle must have the same length L (QEW_EINVAL otherwise).
+ * The line is taken in FP64 (exact for QEW_FP32_SPLIT), transformed by a batched real-to-complex
+ * cuFFT and the mode powers are summed over chains in a fixed order: the result is
+ * deterministic.  Does not advance the state.  S_out: host array of n_modes doubles, written
+ * before the call returns.  The first call makes a cuFFT plan that the handle keeps; every call
+ * allocates a work area of about 8 bytes per site and frees it again (QEW_ENOMEM if that fails).
+ */
+int qew_structure_factor(qew_handle h, int32_t n_modes, double* S_out);
+
 /* qew_reset -- back to the flat start u = 0 at step 0. */
 int qew_reset(qew_handle h);
 

@@ -68,7 +68,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, "-shared", *ARCH, "-Xcompiler", "-fPIC", "-o", tmp, *objs]
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
+    cmd = [cc, "-shared", *ARCH, "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-L", cudalib, "-lcufft",
+           "-Xlinker", "-rpath=" + cudalib]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{res.stderr}")

@@ -47,6 +47,7 @@ SIGNATURES = {
     "qew_set_state": (ctypes.c_int, [_H, _P]),
     "qew_reset": (ctypes.c_int, [_H]),
     "qew_num_sites": (ctypes.c_int, [_H, _P]),
+    "qew_structure_factor": (ctypes.c_int, [_H, ctypes.c_int32, _P]),
     "qew_disorder_values": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32,
                                            _P, _P, ctypes.c_int64, _P]),
     "qew_philox_words": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),

@@ -7,6 +7,7 @@
 // segment of the fused FP32-split kernel never crosses an observation step, so every
 // observation sees exactly the state after that many steps.
 #include <cuda_runtime.h>
+#include <cufft.h>
 
 #include <algorithm>
 #include <cmath>
@@ -120,6 +121,10 @@ struct qew_ctx {
     unsigned long long* d_crossings = nullptr;
     int32_t* d_error = nullptr;   // set by a kernel whose bounded wait gave up
 
+    // structure factor: cuFFT plan of the handle's chain length and batch (made on first use)
+    cufftHandle sq_plan = 0;
+    bool sq_plan_made = false;
+
     // stream owned by the handle (used unless the caller sets one) and the captured observation graph
     cudaStream_t own_stream = nullptr;
     bool use_graphs = true;
@@ -232,6 +237,9 @@ void free_all(qew_ctx* h)
     if (h->h_obs)
         cudaFreeHost(h->h_obs);
     h->h_obs = nullptr;
+    if (h->sq_plan_made)
+        cufftDestroy(h->sq_plan);
+    h->sq_plan_made = false;
 }
 
 int alloc_state(qew_ctx* h)
@@ -1056,6 +1064,65 @@ int qew_set_state(qew_handle h, const double* u_in)
         return fail(h, QEW_EINVAL, "u_in must not be NULL");
     DeviceGuard g(h->device);
     return set_state_impl(h, u_in);
+}
+
+int qew_structure_factor(qew_handle h, int32_t n_modes, double* S_out)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    if (!S_out)
+        return fail(h, QEW_EINVAL, "S_out must not be NULL");
+    const int64_t L = h->L[0];
+    for (int32_t c = 1; c < h->n_chains; ++c)
+        if (h->L[c] != L)
+            return fail(h, QEW_EINVAL, "the structure factor needs chains of one length");
+    if (n_modes < 1 || n_modes > L / 2)
+        return fail(h, QEW_EINVAL, "n_modes must lie in [1, L/2]");
+    DeviceGuard g(h->device);
+    const int32_t Li = static_cast<int32_t>(L);
+    const int32_t B = h->n_chains;
+    if (!h->sq_plan_made) {
+        int n = Li, inembed = 2 * (Li / 2 + 1), onembed = Li / 2 + 1;
+        const cufftResult r = cufftPlanMany(&h->sq_plan, 1, &n, &inembed, 1, inembed, &onembed, 1, onembed, CUFFT_D2Z, B);
+        if (r != CUFFT_SUCCESS)
+            return fail(h, r == CUFFT_ALLOC_FAILED ? QEW_ENOMEM : QEW_ECUDA,
+                        "cuFFT plan of the structure factor failed (status " + std::to_string(static_cast<int>(r)) + ")");
+        h->sq_plan_made = true;
+    }
+    if (cufftSetStream(h->sq_plan, h->stream) != CUFFT_SUCCESS)
+        return fail(h, QEW_ECUDA, "cuFFT could not take the handle's stream");
+    const size_t rows_n = static_cast<size_t>(B) * 2 * (static_cast<size_t>(Li) / 2 + 1);
+    double* d_rows = nullptr;
+    double* d_S = nullptr;
+    int rc = QEW_OK;
+    cudaError_t e = dev_alloc(&d_rows, rows_n);
+    if (e == cudaSuccess)
+        e = dev_alloc(&d_S, static_cast<size_t>(n_modes));
+    if (e != cudaSuccess) {
+        rc = cuda_fail(h, e, "allocating the structure-factor work area");
+    } else {
+        if (h->precision == QEW_FP32_SPLIT)
+            e = sq_rows(h->d_chains, B, Li, &h->sp[h->cur], nullptr, d_rows, h->stream);
+        else
+            e = sq_rows(h->d_chains, B, Li, nullptr, h->u64[h->cur], d_rows, h->stream);
+        if (e == cudaSuccess) {
+            const cufftResult r = cufftExecD2Z(h->sq_plan, d_rows, reinterpret_cast<cufftDoubleComplex*>(d_rows));
+            if (r != CUFFT_SUCCESS)
+                rc = fail(h, QEW_ECUDA, "cuFFT transform failed (status " + std::to_string(static_cast<int>(r)) + ")");
+        }
+        if (rc == QEW_OK && e == cudaSuccess)
+            e = sq_power(d_rows, Li, B, n_modes, d_S, h->stream);
+        if (rc == QEW_OK && e == cudaSuccess)
+            e = cudaMemcpyAsync(S_out, d_S, static_cast<size_t>(n_modes) * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->stream);
+        if (rc == QEW_OK && e == cudaSuccess)
+            e = cudaStreamSynchronize(h->stream);
+        if (rc == QEW_OK && e != cudaSuccess)
+            rc = cuda_fail(h, e, "computing the structure factor");
+    }
+    dev_free(d_rows);
+    dev_free(d_S);
+    return rc;
 }
 
 int qew_reset(qew_handle h)

@@ -84,6 +84,13 @@ cudaError_t f64_cells(const ChainDesc* chains, const TileDesc* tiles, int32_t n_
 cudaError_t reduce_chains(const ChainDesc* chains, int32_t n_chains, const double* partial, double* shift,
                           double* obs, int integer_shift, cudaStream_t stream);
 
+// Structure factor (Eq. 6): rows of u(x) - c0 per chain in the padded layout of an in-place
+// real-to-complex FFT (row stride 2 (L/2 + 1) doubles), from the split state (split != NULL) or
+// the FP64 state; then the mean over chains of |Z(n)|^2 / L^2 for n = 1 .. n_modes.
+cudaError_t sq_rows(const ChainDesc* chains, int32_t n_chains, int32_t L, const SplitState* split, const double* u64,
+                    double* rows, cudaStream_t stream);
+cudaError_t sq_power(const void* Z, int32_t L, int32_t n_chains, int32_t n_modes, double* S, cudaStream_t stream);
+
 // Message returned by qew_last_error(NULL) for calls without a handle (this thread).
 void set_last_error(const std::string& msg);
 

@@ -121,6 +121,15 @@ class Relaxation:
         self._check(self._lib.qew_get_cells(self._h, _ptr(c)))
         return c
 
+    def structure_factor(self, n_modes: int | None = None) -> np.ndarray:
+        """S_q of Eq. 6 at q = 2 pi n / L, n = 1 .. n_modes (default L // 2), averaged over the
+        chains (which must share one length)."""
+        L = int(self.L[0])
+        m = L // 2 if n_modes is None else int(n_modes)
+        out = np.empty(max(m, 0))
+        self._check(self._lib.qew_structure_factor(self._h, m, _ptr(out)))
+        return out
+
     def enable_stats(self, on: bool = True) -> None:
         self._check(self._lib.qew_enable_stats(self._h, 1 if on else 0))
 
