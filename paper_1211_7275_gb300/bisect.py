@@ -2,9 +2,13 @@
 
 Short-time dynamics criterion (arXiv:1211.7275, Sec. III.A): at f_c the velocity decays as a power
 law v ~ t^{-beta/(nu z)}; above f_c it saturates, below it collapses.  Each trial relaxes a batch of
-chains on the GPU and fits the log-log slope of V(t) t^{beta/(nu z)} over the last decade of t
-(beta/(nu z) = 0.128, Sec. IV.E): a slope >= 0 means f is above f_c^L (ties count as above).
-All the control is on the host; every trial is one GPU relaxation through the C ABI.
+chains on the GPU and fits, over the last decade of t, either
+  - "v" (default): the log-log slope of V(t) t^{beta/(nu z)} (beta/(nu z) = 0.128, Sec. IV.E); a
+    slope >= 0 means f is above f_c^L; or
+  - "gamma": the log-log slope of gamma = w / (t v) (Sec. IV.C, IV.F), which needs no exponent; a
+    slope <= 0 means f is above f_c^L.
+Ties count as above.  All the control is on the host; every trial is one GPU relaxation through
+the C ABI.
 """
 from __future__ import annotations
 
@@ -16,6 +20,7 @@ import time
 import numpy as np
 
 from . import relax as _relax
+from . import std as _std
 
 BETA_NU_Z = 0.128
 
@@ -26,7 +31,8 @@ def log_steps(n_steps: int, k: int = 30) -> np.ndarray:
 
 
 def drift(f: float, L: int, batch: int, kind: int, n_steps: int, dt: float = 0.1, seed: int = 12117275,
-          tuning=None) -> float:
+          tuning=None, criterion: str = "v") -> float:
+    """Positive (or zero) when f is above f_c^L, negative below, by the chosen criterion."""
     steps = log_steps(n_steps)
     with _relax.Relaxation(L, f, kind, dt=dt, seed=seed, batch=batch) as r:
         if tuning:
@@ -37,6 +43,8 @@ def drift(f: float, L: int, batch: int, kind: int, n_steps: int, dt: float = 0.1
     sel = t >= t[-1] / 10
     if np.any(V[sel] <= 0):
         return -math.inf
+    if criterion == "gamma":
+        return -_std.gamma_drift(t, V, out["w2"].mean(axis=1))
     return float(np.polyfit(np.log(t[sel]), np.log(V[sel] * t[sel] ** BETA_NU_Z), 1)[0])
 
 
@@ -52,7 +60,7 @@ def bisect(L: int, batch: int, kind: int, n_steps: int, lo: float = 0.5, hi: flo
         else:
             lo = mid
     return {"f_c": 0.5 * (lo + hi), "bracket": [lo, hi], "history": hist, "L": L, "batch": batch, "kind": kind,
-            "n_steps": n_steps, "beta_over_nu_z": BETA_NU_Z}
+            "n_steps": n_steps, "criterion": kw.get("criterion", "v"), "beta_over_nu_z": BETA_NU_Z}
 
 
 def main() -> None:
@@ -64,9 +72,10 @@ def main() -> None:
     p.add_argument("--lo", type=float, default=0.5)
     p.add_argument("--hi", type=float, default=3.0)
     p.add_argument("--iters", type=int, default=15)
+    p.add_argument("--criterion", choices=["v", "gamma"], default="v")
     a = p.parse_args()
     t0 = time.time()
-    res = bisect(a.L, a.batch, a.kind, a.n_steps, a.lo, a.hi, a.iters)
+    res = bisect(a.L, a.batch, a.kind, a.n_steps, a.lo, a.hi, a.iters, criterion=a.criterion)
     res["seconds"] = time.time() - t0
     print(json.dumps(res))
 

@@ -238,3 +238,39 @@ def test_full_size_case3_4x2e25(qew, orc):
             assert abs(u[c * L + i] - ref_u[0]) <= 1e-4, (c, i, u[c * L + i], ref_u[0])
     dub = obs["ubar"][2] - obs["ubar"][1]
     assert np.all(np.abs(dub - 0.1 * obs["v"][1]) <= 2e-6 * np.maximum(1, np.abs(obs["ubar"][1])))
+
+
+def test_case3_at_the_paper_size_follows_the_printed_fits(qew):
+    """Case 3 at the paper's largest run (4 x 2^25 sites, f_c = 1.5652, dt = 0.1, Sec. IV.D), 10^4
+    steps: V(t) within 3% of the printed v = 0.721 t^-0.128 [1 + (t/0.110)^-0.715] for t >= 1.5,
+    and the corrected-form fits of V and w (procedure (a) of Sec. IV.E, t_mic = 2) give exponents
+    near the printed beta/nu z = 1 - zeta/z = 0.128."""
+    from paper_1211_7275_gb300 import std
+    steps = log_spaced_steps(10_000, 60)
+    with qew.Relaxation(1 << 25, 1.5652, RBG_LINEAR, dt=0.1, seed=SEED, batch=4) as r:
+        r.set_tuning(0, 0, 0)
+        obs = r.observe(steps)
+    t = steps * 0.1
+    V, W2 = obs["v"].mean(1), obs["w2"].mean(1)
+    sel = t >= 1.5
+    ratio = V[sel] / std.corrected(t[sel], 0.721, -0.128, 0.110, 0.715)
+    print(f"Case 3 at 4 x 2^25: V / printed fit in [{ratio.min():.4f}, {ratio.max():.4f}]")
+    assert np.all(np.abs(ratio - 1) < 0.03)
+    fv = std.fit_corrected(t, V, t_mic=2.0)
+    fw = std.fit_corrected(t, np.sqrt(W2), t_mic=2.0)
+    print(f"corrected fits: beta/nu z = {-fv['e']:.4f} (V0 {fv['A']:.3f}), zeta/z = {fw['e']:.4f}")
+    assert 0.115 <= -fv["e"] <= 0.14
+    assert 0.82 <= fw["e"] <= 0.95
+
+
+
+@pytest.mark.parametrize("criterion", ["v", "gamma"])
+def test_bisection_criteria_bracket_the_threshold(qew, criterion):
+    """Both bisection criteria (the V t^0.128 slope and the gamma drift of Sec. IV.F) call a drive
+    20% above the random-field f_c^L of the 16 x 2^20 preset "above" and 20% below "below"."""
+    from paper_1211_7275_gb300 import bisect
+    from qew_workloads import preset_f
+    fc = preset_f("rf_16x2^20")
+    up = bisect.drift(1.2 * fc, 1 << 16, 8, RF, 4096, criterion=criterion)
+    down = bisect.drift(0.8 * fc, 1 << 16, 8, RF, 4096, criterion=criterion)
+    assert up >= 0 > down, (up, down)
