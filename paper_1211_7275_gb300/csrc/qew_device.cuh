@@ -111,40 +111,82 @@ __device__ __forceinline__ uint4 disorder_words(uint64_t seed, uint32_t s, int32
                          static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
 }
 
-// cos(2 pi (x + 1/2) 2^-32) in FP32 with an exact argument.  Rounding U2 = (x + 1/2) 2^-32 to
-// FP32 would move the angle by up to 2 pi 2^-24; instead split 2 U2 = h + l with
-// h = (x >> 16) 2^-15 and l = ((x mod 2^16) + 1/2) 2^-31 (both exact in FP32, l < 2^-15), take
-// sin/cos(pi h) from sincospif, and add the small angle pi l by the angle-addition formula with
-// sin(pi l) = pi l and cos(pi l) = 1 - (pi l)^2 / 2 (the next terms are below FP32 resolution).
+// ln U1 for U1 = (x + 1/2) 2^-32, in FP32, from the odd series of the inverse hyperbolic tangent,
+// 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + ...), with s in [0, 1/3] in both halves:
+//   x < 2^31:   U1 = 2^e m with m in [1, 2) read from the float's bits, and
+//               ln U1 = e ln 2 + ln m,  ln m = 2 atanh((m - 1) / (m + 1));
+//   x >= 2^31:  1 - U1 = t = (~x + 1/2) 2^-32 is exact in the word arithmetic, and
+//               ln U1 = ln(1 - t) = -2 atanh(t / (2 - t)),
+// so values of U1 near 1 keep their relative accuracy (forming 1 - U1 from a rounded U1 would
+// cancel).  Nine terms reach FP32 resolution for s <= 1/3 (the next is below 3e-9 s).  Both
+// halves are evaluated and selected, so a warp of mixed words does not diverge; the quotient is
+// an approximate reciprocal refined by one Newton step.
+__device__ __forceinline__ float ln_u1_f32(uint32_t x)
+{
+    const bool upper = (x & 0x80000000u) != 0;
+    const float u1 = fmaf(static_cast<float>(x), 0x1p-32f, 0x1p-33f);
+    const uint32_t bits = __float_as_uint(u1);
+    const float m = __uint_as_float((bits & 0x007FFFFFu) | 0x3F800000u);   // exact
+    const float e = static_cast<float>(static_cast<int>(bits >> 23) - 127);
+    const float t = fmaf(static_cast<float>(~x), 0x1p-32f, 0x1p-33f);
+    const float num = upper ? t : m - 1.0f;
+    const float den = upper ? 2.0f - t : m + 1.0f;
+    const float rc = __fdividef(1.0f, den);
+    const float s0 = num * rc;
+    const float s = fmaf(fmaf(-s0, den, num), rc, s0);   // one Newton correction of num / den
+    const float z = s * s;
+    float p = 1.0f / 17.0f;
+    p = fmaf(p, z, 1.0f / 15.0f);
+    p = fmaf(p, z, 1.0f / 13.0f);
+    p = fmaf(p, z, 1.0f / 11.0f);
+    p = fmaf(p, z, 1.0f / 9.0f);
+    p = fmaf(p, z, 1.0f / 7.0f);
+    p = fmaf(p, z, 1.0f / 5.0f);
+    p = fmaf(p, z, 1.0f / 3.0f);
+    p = fmaf(p, z, 1.0f);
+    const float at2 = 2.0f * s * p;   // 2 atanh(s)
+    return upper ? -at2 : fmaf(e, 0.693147180559945f, at2);
+}
+
+// cos(2 pi U2) for U2 = (x + 1/2) 2^-32, in FP32.  The octant k = x >> 29 and, within it, the
+// distance to the nearest multiple of pi/2 (in units of pi/4, formed exactly from the low 29 bits)
+// reduce the angle to theta in (0, pi/4); cos(2 pi U2) is then +-cos(theta) or +-sin(theta), from
+// their Taylor polynomials (truncation below 2e-9).  The reduction is exact, so the result keeps
+// a relative accuracy of about 1e-7 also near the zeros of the cosine.
 __device__ __forceinline__ float cos_2pi_word(uint32_t x)
 {
-    const float h = static_cast<float>(x >> 16) * 0x1p-15f;
-    const float l = fmaf(static_cast<float>(x & 0xFFFFu), 0x1p-31f, 0x1p-32f);
-    float s, c;
-    sincospif(h, &s, &c);
-    const float pl = 3.14159265358979f * l;
-    return fmaf(-s, pl, fmaf(-0.5f * pl, pl * c, c));
+    const uint32_t k = x >> 29;
+    const uint32_t r = x & 0x1FFFFFFFu;
+    const uint32_t q = (k & 1u) ? (0x1FFFFFFFu - r) : r;
+    const float th = fmaf(static_cast<float>(q), 0x1p-29f, 0x1p-30f) * 0.785398163397448f;
+    const float z = th * th;
+    float sp = 1.0f / 362880.0f;
+    sp = fmaf(sp, z, -1.0f / 5040.0f);
+    sp = fmaf(sp, z, 1.0f / 120.0f);
+    sp = fmaf(sp, z, -1.0f / 6.0f);
+    const float sn = fmaf(sp * z, th, th);
+    float cp = -1.0f / 3628800.0f;
+    cp = fmaf(cp, z, 1.0f / 40320.0f);
+    cp = fmaf(cp, z, -1.0f / 720.0f);
+    cp = fmaf(cp, z, 1.0f / 24.0f);
+    cp = fmaf(cp, z, -0.5f);
+    const float cs = fmaf(cp, z, 1.0f);
+    const float v = (((k + 1u) >> 1) & 1u) ? sn : cs;   // octants 1, 2, 5, 6 take the sine
+    return (((k + 2u) >> 2) & 1u) ? -v : v;             // octants 2 .. 5 are negative
 }
 
 // N(0, 1) value sqrt(-2 ln U1) cos(2 pi U2), U_k = (x_k + 1/2) 2^-32 (Box-Muller, cosine
-// branch): the random-field force R and the Gaussian random-bond potential G.
-// FP32: ln U1 is taken as log1p(-(1 - U1)) when U1 > 1/2, where 1 - U1 = (~x0 + 1/2) 2^-32 is
-// exact in the word arithmetic; this keeps the small values of R near U1 -> 1 accurate
-// (rounding U1 itself to FP32 would flush them to zero).
-// One log1pf for both halves, so a warp evaluating many values does not diverge: for U1 < 1/2,
-// U1 = m 2^e with m in [1, 2) read from the float's bits and ln U1 = e ln 2 + log1p(m - 1).
-// The value plus `add` is rounded once (the random-field cache holds R + f), by an explicit fused
-// multiply-add, so every kernel that draws a value rounds it the same way.
+// branch): the random-field force R and the Gaussian random-bond potential G.  The value plus
+// `add` is rounded once (the random-field cache holds R + f), by an explicit fused multiply-add,
+// so every kernel that draws a value rounds it the same way.  -2 ln U1 > 0 always (U1 < 1), so
+// its square root is a rsqrt(a), refined by one Newton step.
 __device__ __forceinline__ float gauss_value_plus_f32(uint4 w, float add)
 {
-    const bool upper = (w.x & 0x80000000u) != 0;
-    const float u1 = fmaf(static_cast<float>(w.x), 0x1p-32f, 0x1p-33f);
-    const uint32_t bits = __float_as_uint(u1);
-    const float m1 = __uint_as_float((bits & 0x007FFFFFu) | 0x3F800000u) - 1.0f;   // exact
-    const float e = static_cast<float>(static_cast<int>(bits >> 23) - 127);
-    const float t = upper ? -fmaf(static_cast<float>(~w.x), 0x1p-32f, 0x1p-33f) : m1;
-    const float lg = fmaf(upper ? 0.0f : e, 0.693147180559945f, log1pf(t));
-    return __fmaf_rn(sqrtf(-2.0f * lg), cos_2pi_word(w.y), add);
+    const float a = -2.0f * ln_u1_f32(w.x);
+    const float y = rsqrtf(a);
+    const float r0 = a * y;
+    const float r = fmaf(fmaf(-r0, r0, a), 0.5f * y, r0);   // one Newton correction of sqrt(a)
+    return __fmaf_rn(r, cos_2pi_word(w.y), add);
 }
 
 __device__ __forceinline__ float gauss_value_f32(uint4 w)
