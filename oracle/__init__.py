@@ -11,7 +11,8 @@ Functions and the passages they follow:
                      name its generator (Sec. III.B), this is the reading used throughout.
   disorder_values    R(s,i,n) ~ N(0,1) (RF), V(s,i,n) ~ U(-1,1) (RB) or G(s,i,n) ~ N(0,1)
                      (Gaussian RB, Cases 1 and 3) drawn at integer (i,n), Sec. III.B and the
-                     disorder cases of Sec. IV.C.
+                     disorder cases of Sec. IV.C; optionally periodic in n with period M (the
+                     L x M system of Sec. III.B).
   pinning_force      F_p(i,u): linear interpolation of R (RF), -dV/du of the Catmull-Rom
                      spline through V (RB) or G (Case 1), or -dV/du of the linear spline
                      through G (Case 3), Sec. III.B and Sec. IV.C.
@@ -67,20 +68,20 @@ def _load():
             lib.oracle_philox4x32_10.argtypes = [P, P, ctypes.c_int64, P]
             lib.oracle_philox4x32_10.restype = None
             lib.oracle_disorder_values.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, P, P,
-                                                   ctypes.c_int64, P]
+                                                   ctypes.c_int64, P, ctypes.c_int64]
             lib.oracle_disorder_values.restype = None
             lib.oracle_pinning_force.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, P, P,
-                                                 ctypes.c_int64, P]
+                                                 ctypes.c_int64, P, ctypes.c_int64]
             lib.oracle_pinning_force.restype = None
             lib.oracle_rb_potential.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, P, P,
-                                                ctypes.c_int64, P]
+                                                ctypes.c_int64, P, ctypes.c_int64]
             lib.oracle_rb_potential.restype = None
             lib.oracle_run.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.c_double, ctypes.c_uint64, P, P,
-                                       ctypes.c_int32, P, P, P, P, ctypes.c_int32]
+                                       ctypes.c_int32, P, P, P, P, ctypes.c_int32, ctypes.c_int64]
             lib.oracle_run.restype = ctypes.c_int
             lib.oracle_lightcone.argtypes = [ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
-                                             ctypes.c_int64, P, P]
+                                             ctypes.c_int64, P, P, ctypes.c_int64]
             lib.oracle_lightcone.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -101,41 +102,43 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     return out
 
 
-def disorder_values(kind: int, seed: int, s: int, i, n) -> np.ndarray:
-    """R(s,i,n) for RF, V(s,i,n) for RB, G(s,i,n) for the Gaussian RB kinds, at integer (i, n)."""
+def disorder_values(kind: int, seed: int, s: int, i, n, period: int = 0) -> np.ndarray:
+    """R(s,i,n) for RF, V(s,i,n) for RB, G(s,i,n) for the Gaussian RB kinds, at integer (i, n)
+    (n taken mod ``period`` when it is positive)."""
     i = np.ascontiguousarray(i, dtype=np.int64).ravel()
     n = np.ascontiguousarray(n, dtype=np.int64).ravel()
     out = np.empty(i.shape[0], np.float64)
-    _load().oracle_disorder_values(kind, seed, s, _p(i), _p(n), i.shape[0], _p(out))
+    _load().oracle_disorder_values(kind, seed, s, _p(i), _p(n), i.shape[0], _p(out), period)
     return out
 
 
-def pinning_force(kind: int, seed: int, s: int, i, u) -> np.ndarray:
+def pinning_force(kind: int, seed: int, s: int, i, u, period: int = 0) -> np.ndarray:
     """F_p(i, u) of chain ``s`` for each (i, u) pair."""
     i = np.ascontiguousarray(i, dtype=np.int64).ravel()
     u = np.ascontiguousarray(u, dtype=np.float64).ravel()
     out = np.empty(i.shape[0], np.float64)
-    _load().oracle_pinning_force(kind, seed, s, _p(i), _p(u), i.shape[0], _p(out))
+    _load().oracle_pinning_force(kind, seed, s, _p(i), _p(u), i.shape[0], _p(out), period)
     return out
 
 
-def rb_potential(seed: int, s: int, i, u, kind: int = KIND_RB) -> np.ndarray:
+def rb_potential(seed: int, s: int, i, u, kind: int = KIND_RB, period: int = 0) -> np.ndarray:
     """RB potential V(i, u) of chain ``s``: Catmull-Rom (RB, Case 1) or linear (Case 3)."""
     i = np.ascontiguousarray(i, dtype=np.int64).ravel()
     u = np.ascontiguousarray(u, dtype=np.float64).ravel()
     out = np.empty(i.shape[0], np.float64)
-    _load().oracle_rb_potential(kind, seed, s, _p(i), _p(u), i.shape[0], _p(out))
+    _load().oracle_rb_potential(kind, seed, s, _p(i), _p(u), i.shape[0], _p(out), period)
     return out
 
 
 def run(L, f, dt: float, kind, seed: int, steps, *, s=None, u0=None, n_threads: int = 0,
-        want_state: bool = False) -> dict:
+        want_state: bool = False, period: int = 0) -> dict:
     """Relax independent periodic chains and observe them at ``steps``.
 
     ``L``, ``f``, ``kind`` and ``s`` are per-chain sequences (scalars broadcast); ``s``
     defaults to 0..n_chains-1.  ``u0`` is the concatenated initial state (default: flat).
     Returns ``v``, ``ubar``, ``w2`` as [n_times, n_chains] and, with ``want_state``, the
-    concatenated final state ``u``.
+    concatenated final state ``u``.  ``period`` > 0 makes the disorder periodic in u with that
+    period (the L x M system of Sec. III.B).
     """
     L = np.atleast_1d(np.asarray(L, dtype=np.int64))
     n_chains = L.shape[0]
@@ -158,7 +161,8 @@ def run(L, f, dt: float, kind, seed: int, steps, *, s=None, u0=None, n_threads: 
     u_out = np.empty(total) if want_state else None
     rc = _load().oracle_run(n_chains, _p(L), _p(s), _p(f), _p(kind), dt, seed,
                             _p(u_in) if u_in is not None else None, _p(steps), nt,
-                            _p(v), _p(ub), _p(w2), _p(u_out) if u_out is not None else None, n_threads)
+                            _p(v), _p(ub), _p(w2), _p(u_out) if u_out is not None else None, n_threads,
+                            int(period))
     if rc != 0:
         raise ValueError(f"oracle_run failed with status {rc}")
     out = {"v": v, "ubar": ub, "w2": w2}
@@ -168,11 +172,11 @@ def run(L, f, dt: float, kind, seed: int, steps, *, s=None, u0=None, n_threads: 
 
 
 def lightcone(L: int, s: int, f: float, dt: float, kind: int, seed: int, i0: int, w: int,
-              n_steps: int) -> tuple[np.ndarray, np.ndarray]:
+              n_steps: int, period: int = 0) -> tuple[np.ndarray, np.ndarray]:
     """u and F_p at sites i0..i0+w-1 (mod L) of chain ``s`` after ``n_steps`` from the flat start."""
     u = np.empty(w)
     F = np.empty(w)
-    rc = _load().oracle_lightcone(L, s, f, dt, kind, seed, i0, w, n_steps, _p(u), _p(F))
+    rc = _load().oracle_lightcone(L, s, f, dt, kind, seed, i0, w, n_steps, _p(u), _p(F), int(period))
     if rc != 0:
         raise ValueError(f"oracle_lightcone failed with status {rc}")
     return u, F

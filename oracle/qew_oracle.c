@@ -25,6 +25,9 @@
  *     RB-G cubic (Case 1):        F = -dV/du, V the Catmull-Rom spline through
  *                                 G(i, n-1 .. n+2),  G ~ N(0, 1)
  *   with n = floor(u), d = u - n.
+ *   Periodic disorder (the L x M system of Sec. III.B): with a period M > 0 every node index n
+ *   is taken mod M (in [0, M)) before it keys the generator, so the disorder repeats in u
+ *   with period M; M = 0 leaves it aperiodic (the memory-free runs of Sec. IV.D).
  *   Observables (Sec. II, Eqs. 3-5): v = f + (1/L) sum_i F_i at the observed state (the
  *   periodic Laplacian sums to zero), ubar = (1/L) sum_i u_i, w2 = (1/L) sum_i (u_i-ubar)^2.
  *   Flat start u_i(0) = 0 (Sec. II).
@@ -103,6 +106,16 @@ static void disorder_words(uint64_t seed, uint32_t s, int64_t i, int64_t n, uint
     philox4x32_10(ctr, key, w);
 }
 
+/* Node index of a disorder periodic in u with period M (the L x M system of Sec. III.B):
+   n mod M in [0, M); M <= 0 leaves the disorder aperiodic. */
+static int64_t wrap_node(int64_t n, int64_t period)
+{
+    if (period <= 0)
+        return n;
+    int64_t r = n % period;
+    return r < 0 ? r + period : r;
+}
+
 /* N(0, 1) value from two output words: Box-Muller, cosine branch. */
 static double box_muller(const uint32_t w[4])
 {
@@ -137,13 +150,14 @@ static double rb_value(uint64_t seed, uint32_t s, int64_t i, int64_t n)
 }
 
 /* Potential value at an integer point for the RB kinds. */
-static double potential_value(int kind, uint64_t seed, uint32_t s, int64_t i, int64_t n)
+static double potential_value(int kind, uint64_t seed, uint32_t s, int64_t i, int64_t n, int64_t period)
 {
+    n = wrap_node(n, period);
     return kind == QO_RB ? rb_value(seed, s, i, n) : rbg_value(seed, s, i, n);
 }
 
 /* Pinning force at site i of chain s and displacement u (Sec. III.B, Sec. IV.C). */
-static double pinning_force(int kind, uint64_t seed, uint32_t s, int64_t i, double u)
+static double pinning_force(int kind, uint64_t seed, uint32_t s, int64_t i, double u, int64_t period)
 {
     if (kind == QO_NONE)
         return 0.0;
@@ -151,22 +165,22 @@ static double pinning_force(int kind, uint64_t seed, uint32_t s, int64_t i, doub
     int64_t n = (int64_t)fl;
     double d = u - fl;
     if (kind == QO_RF) {
-        double r0 = rf_value(seed, s, i, n);
-        double r1 = rf_value(seed, s, i, n + 1);
+        double r0 = rf_value(seed, s, i, wrap_node(n, period));
+        double r1 = rf_value(seed, s, i, wrap_node(n + 1, period));
         return (1.0 - d) * r0 + d * r1;
     }
     if (kind == QO_RBG_LINEAR) {
         /* V(u) = (1 - d) G(n) + d G(n+1) on [n, n+1), so -dV/du = G(n) - G(n+1) */
-        return rbg_value(seed, s, i, n) - rbg_value(seed, s, i, n + 1);
+        return rbg_value(seed, s, i, wrap_node(n, period)) - rbg_value(seed, s, i, wrap_node(n + 1, period));
     }
     /* RB / RB-G cubic: V(u) on [n, n+1] is the uniform Catmull-Rom cubic through
        p0..p3 = V(n-1..n+2):
        V(d) = 1/2 [2 p1 + (p2 - p0) d + (2p0 - 5p1 + 4p2 - p3) d^2 + (-p0 + 3p1 - 3p2 + p3) d^3]
        and F = -dV/du. */
-    double p0 = potential_value(kind, seed, s, i, n - 1);
-    double p1 = potential_value(kind, seed, s, i, n);
-    double p2 = potential_value(kind, seed, s, i, n + 1);
-    double p3 = potential_value(kind, seed, s, i, n + 2);
+    double p0 = potential_value(kind, seed, s, i, n - 1, period);
+    double p1 = potential_value(kind, seed, s, i, n, period);
+    double p2 = potential_value(kind, seed, s, i, n + 1, period);
+    double p3 = potential_value(kind, seed, s, i, n + 2, period);
     double a = p2 - p0;
     double b = ((2.0 * p0 - 5.0 * p1) + 4.0 * p2) - p3;
     double c = ((3.0 * p1 - p0) - 3.0 * p2) + p3;
@@ -175,17 +189,17 @@ static double pinning_force(int kind, uint64_t seed, uint32_t s, int64_t i, doub
 
 /* The RB potential itself, V(i, u), for the spline pins: Catmull-Rom (RB, RB-G cubic) or
    linear (RB-G linear). */
-static double rb_potential(int kind, uint64_t seed, uint32_t s, int64_t i, double u)
+static double rb_potential(int kind, uint64_t seed, uint32_t s, int64_t i, double u, int64_t period)
 {
     double fl = floor(u);
     int64_t n = (int64_t)fl;
     double d = u - fl;
     if (kind == QO_RBG_LINEAR)
-        return (1.0 - d) * rbg_value(seed, s, i, n) + d * rbg_value(seed, s, i, n + 1);
-    double p0 = potential_value(kind, seed, s, i, n - 1);
-    double p1 = potential_value(kind, seed, s, i, n);
-    double p2 = potential_value(kind, seed, s, i, n + 1);
-    double p3 = potential_value(kind, seed, s, i, n + 2);
+        return (1.0 - d) * rbg_value(seed, s, i, wrap_node(n, period)) + d * rbg_value(seed, s, i, wrap_node(n + 1, period));
+    double p0 = potential_value(kind, seed, s, i, n - 1, period);
+    double p1 = potential_value(kind, seed, s, i, n, period);
+    double p2 = potential_value(kind, seed, s, i, n + 1, period);
+    double p3 = potential_value(kind, seed, s, i, n + 2, period);
     double a = p2 - p0;
     double b = ((2.0 * p0 - 5.0 * p1) + 4.0 * p2) - p3;
     double c = ((3.0 * p1 - p0) - 3.0 * p2) + p3;
@@ -193,26 +207,28 @@ static double rb_potential(int kind, uint64_t seed, uint32_t s, int64_t i, doubl
 }
 
 void oracle_disorder_values(int kind, uint64_t seed, uint32_t s, const int64_t* i, const int64_t* n,
-                            int64_t count, double* out)
+                            int64_t count, double* out, int64_t period)
 {
-    for (int64_t k = 0; k < count; ++k)
-        out[k] = (kind == QO_RF) ? rf_value(seed, s, i[k], n[k])
-                 : (kind == QO_RB) ? rb_value(seed, s, i[k], n[k])
-                                   : rbg_value(seed, s, i[k], n[k]);
+    for (int64_t k = 0; k < count; ++k) {
+        int64_t m = wrap_node(n[k], period);
+        out[k] = (kind == QO_RF) ? rf_value(seed, s, i[k], m)
+                 : (kind == QO_RB) ? rb_value(seed, s, i[k], m)
+                                   : rbg_value(seed, s, i[k], m);
+    }
 }
 
 void oracle_pinning_force(int kind, uint64_t seed, uint32_t s, const int64_t* i, const double* u,
-                          int64_t count, double* out)
+                          int64_t count, double* out, int64_t period)
 {
     for (int64_t k = 0; k < count; ++k)
-        out[k] = pinning_force(kind, seed, s, i[k], u[k]);
+        out[k] = pinning_force(kind, seed, s, i[k], u[k], period);
 }
 
 void oracle_rb_potential(int kind, uint64_t seed, uint32_t s, const int64_t* i, const double* u, int64_t count,
-                         double* out)
+                         double* out, int64_t period)
 {
     for (int64_t k = 0; k < count; ++k)
-        out[k] = rb_potential(kind, seed, s, i[k], u[k]);
+        out[k] = rb_potential(kind, seed, s, i[k], u[k], period);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -263,6 +279,7 @@ typedef struct {
     double f, dt;
     int kind;
     uint64_t seed;
+    int64_t period;        /* disorder period M in u (0: aperiodic) */
     const double* u0;      /* initial state [L] or NULL for the flat start */
     const int64_t* steps;  /* observation steps, strictly increasing, >= 0 */
     int32_t n_times;
@@ -291,7 +308,7 @@ static int run_chain(chain_job_t* job)
         int64_t target = job->steps[k];
         for (;;) {
             for (int64_t i = 0; i < L; ++i)
-                F[i] = pinning_force(job->kind, job->seed, job->s, i, u[i]);
+                F[i] = pinning_force(job->kind, job->seed, job->s, i, u[i], job->period);
             if (step == target)
                 break;
             for (int64_t i = 0; i < L; ++i) {
@@ -370,14 +387,16 @@ static int run_jobs(chain_job_t* jobs, int32_t n_jobs, int32_t n_threads)
 
 /*
  * Run n_chains independent chains; chain c has length L[c], sample index s[c], drive f[c]
- * and disorder kind kind[c].  Observations at steps[0..n_times) are written to
+ * and disorder kind kind[c]; the disorder is periodic in u with period `period` (0:
+ * aperiodic).  Observations at steps[0..n_times) are written to
  * v_out/ubar_out/w2_out[k * n_chains + c].  u0 (optional) and u_final (optional) hold the
  * chains one after another (chain c starts at offset sum_{c'<c} L[c']).
  * Returns 0, or -1 on bad arguments, -2 on allocation failure.
  */
 int oracle_run(int32_t n_chains, const int64_t* L, const uint32_t* s, const double* f, const int32_t* kind,
                double dt, uint64_t seed, const double* u0, const int64_t* steps, int32_t n_times,
-               double* v_out, double* ubar_out, double* w2_out, double* u_final, int32_t n_threads)
+               double* v_out, double* ubar_out, double* w2_out, double* u_final, int32_t n_threads,
+               int64_t period)
 {
     if (n_chains < 1 || n_times < 0)
         return -1;
@@ -399,6 +418,7 @@ int oracle_run(int32_t n_chains, const int64_t* L, const uint32_t* s, const doub
         jobs[c].dt = dt;
         jobs[c].kind = kind[c];
         jobs[c].seed = seed;
+        jobs[c].period = period;
         jobs[c].u0 = u0 ? u0 + off : NULL;
         jobs[c].steps = steps;
         jobs[c].n_times = n_times;
@@ -423,7 +443,7 @@ int oracle_run(int32_t n_chains, const int64_t* L, const uint32_t* s, const doub
  * force at that state.  Returns 0, -1 on bad arguments, -2 on allocation failure.
  */
 int oracle_lightcone(int64_t L, uint32_t s, double f, double dt, int kind, uint64_t seed, int64_t i0,
-                     int64_t w, int64_t n_steps, double* u_out, double* F_out)
+                     int64_t w, int64_t n_steps, double* u_out, double* F_out, int64_t period)
 {
     if (L < 1 || w < 1 || n_steps < 0 || w + 2 * n_steps > L)
         return -1;
@@ -443,7 +463,7 @@ int oracle_lightcone(int64_t L, uint32_t s, double f, double dt, int kind, uint6
     for (int64_t k = 0; k < n_steps; ++k) {
         /* sites k .. W-1-k are exact before this step; k+1 .. W-2-k after it */
         for (int64_t j = k; j <= W - 1 - k; ++j)
-            F[j] = pinning_force(kind, seed, s, gi[j], u[j]);
+            F[j] = pinning_force(kind, seed, s, gi[j], u[j], period);
         for (int64_t j = k + 1; j <= W - 2 - k; ++j) {
             double lap = (u[j + 1] + u[j - 1]) - 2.0 * u[j];
             un[j] = u[j] + dt * ((lap + f) + F[j]);
@@ -454,7 +474,7 @@ int oracle_lightcone(int64_t L, uint32_t s, double f, double dt, int kind, uint6
     for (int64_t j = 0; j < w; ++j) {
         u_out[j] = u[n_steps + j];
         if (F_out)
-            F_out[j] = pinning_force(kind, seed, s, gi[n_steps + j], u[n_steps + j]);
+            F_out[j] = pinning_force(kind, seed, s, gi[n_steps + j], u[n_steps + j], period);
     }
     free(u); free(un); free(F); free(gi);
     return 0;
