@@ -100,6 +100,17 @@ int qew_set_precision(qew_handle h, int32_t precision);
 int qew_set_stream(qew_handle h, void* stream);
 
 /*
+ * qew_set_disorder_period -- make the disorder of every chain periodic in u with period M (the
+ * periodic L x M samples of Sec. III.B; the paper notes that the memory-free generator can be
+ * forced to be periodic as well): every node index n keys the generator as n mod M, in [0, M).
+ * period = 0 (the default) restores the aperiodic disorder of the memory-free runs (Sec. IV.D).
+ * The state is reset to the flat start at step 0, since every cache depends on the period.
+ * QEW_EINVAL unless 0 <= period < 2^31.  (qew_observe_state_noalloc and qew_disorder_values take
+ * node indices as given, i.e. aperiodic.)
+ */
+int qew_set_disorder_period(qew_handle h, int64_t period);
+
+/*
  * qew_set_tuning -- launch shape of the fused FP32-split kernel: `tile_w` sites per warp tile
  * (32 lanes x an odd number of sites: 224, 480, 736 or 992; random-bond chains 224 or 480),
  * `K` Euler steps per HBM round trip (temporal-block depth, 1 <= K <= tile_w / 4),

@@ -83,6 +83,7 @@ struct qew_ctx {
     int64_t step = 0;
     int kinds_mask = 0;
     int n_cache = 2;
+    int32_t period = 0;   // disorder period M in u (0: aperiodic)
 
     // launch shape of the fused kernel (defaults: the best measured shapes on a GB300)
     int S = 23, K = 16, tpc = 2;
@@ -288,6 +289,7 @@ int build_layout(qew_ctx* h)
         d.s = static_cast<uint32_t>(c);
         d.kind = h->kind[c];
         d.f32 = static_cast<float>(h->f[c]);
+        d.period = h->period;
         d.f64 = h->f[c];
         for (int32_t st = 0; st < d.L; st += kBlockTile)
             blocks.push_back(TileDesc{c, st});
@@ -948,6 +950,21 @@ int qew_set_precision(qew_handle h, int32_t precision)
     int rc = build_layout(h);
     if (rc == QEW_OK)
         rc = alloc_state(h);
+    if (rc == QEW_OK)
+        rc = init_state(h, nullptr, std::vector<double>(h->n_chains, 0.0));
+    return rc;
+}
+
+int qew_set_disorder_period(qew_handle h, int64_t period)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    if (period < 0 || period >= (int64_t(1) << 31))
+        return fail(h, QEW_EINVAL, "period must lie in [0, 2^31)");
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    h->period = static_cast<int32_t>(period);
+    int rc = build_layout(h);
     if (rc == QEW_OK)
         rc = init_state(h, nullptr, std::vector<double>(h->n_chains, 0.0));
     return rc;

@@ -41,8 +41,19 @@ struct ChainDesc {
     int32_t tile0;    // first partial-sum slot of this chain (tiles of its list)
     int32_t ntiles;   // number of tiles (partial-sum slots) of this chain
     float f32;        // drive f, FP32
+    int32_t period;   // disorder period M in u (node index taken mod M); 0: aperiodic
     double f64;       // drive f, FP64
 };
+
+// Node index that keys the generator: n itself, or n mod M in [0, M) for a disorder periodic in
+// u with period M (the L x M system of Sec. III.B).
+__host__ __device__ __forceinline__ int32_t wrap_node(int32_t n, int32_t period)
+{
+    if (period <= 0)
+        return n;
+    const int32_t r = n % period;
+    return r < 0 ? r + period : r;
+}
 
 // One warp tile of the fused kernel (or one block tile of the FP64 kernels): chain and first
 // owned site.

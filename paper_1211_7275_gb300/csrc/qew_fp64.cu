@@ -16,9 +16,11 @@ namespace qew {
 namespace {
 
 // One disorder node in FP64: R (RF), V (uniform random bond) or G (Gaussian random bond).
+// (n is the cell-relative node index; `period` > 0 makes the disorder periodic in u)
 template <int KIND>
-__device__ __forceinline__ double node_f64(uint64_t seed, uint32_t s, int32_t i, int32_t n)
+__device__ __forceinline__ double node_f64(uint64_t seed, uint32_t s, int32_t i, int32_t n, int32_t period)
 {
+    n = wrap_node(n, period);
     if constexpr (KIND == kRF)
         return rf_f64(seed, s, i, n);
     else if constexpr (KIND == kRB)
@@ -29,7 +31,7 @@ __device__ __forceinline__ double node_f64(uint64_t seed, uint32_t s, int32_t i,
 
 template <int KIND>
 __device__ __forceinline__ double pinning_f64(double u, int64_t p, int32_t i, uint32_t s, uint64_t seed,
-                                              const F64State& st)
+                                              const F64State& st, int32_t period)
 {
     if constexpr (KIND == kNone) {
         return 0.0;
@@ -46,13 +48,13 @@ __device__ __forceinline__ double pinning_f64(double u, int64_t p, int32_t i, ui
             } else {
                 if (n == nc + 1) {
                     r0 = st.c[1][p];
-                    r1 = node_f64<KIND>(seed, s, i, n + 1);
+                    r1 = node_f64<KIND>(seed, s, i, n + 1, period);
                 } else if (n == nc - 1) {
                     r1 = st.c[0][p];
-                    r0 = node_f64<KIND>(seed, s, i, n);
+                    r0 = node_f64<KIND>(seed, s, i, n, period);
                 } else {
-                    r0 = node_f64<KIND>(seed, s, i, n);
-                    r1 = node_f64<KIND>(seed, s, i, n + 1);
+                    r0 = node_f64<KIND>(seed, s, i, n, period);
+                    r1 = node_f64<KIND>(seed, s, i, n + 1, period);
                 }
                 st.ncache[p] = n;
                 st.c[0][p] = r0;
@@ -74,17 +76,17 @@ __device__ __forceinline__ double pinning_f64(double u, int64_t p, int32_t i, ui
                     p0 = st.c[1][p];
                     p1 = st.c[2][p];
                     p2 = st.c[3][p];
-                    p3 = node_f64<KIND>(seed, s, i, n + 2);
+                    p3 = node_f64<KIND>(seed, s, i, n + 2, period);
                 } else if (n == nc - 1) {
                     p1 = st.c[0][p];
                     p2 = st.c[1][p];
                     p3 = st.c[2][p];
-                    p0 = node_f64<KIND>(seed, s, i, n - 1);
+                    p0 = node_f64<KIND>(seed, s, i, n - 1, period);
                 } else {
-                    p0 = node_f64<KIND>(seed, s, i, n - 1);
-                    p1 = node_f64<KIND>(seed, s, i, n);
-                    p2 = node_f64<KIND>(seed, s, i, n + 1);
-                    p3 = node_f64<KIND>(seed, s, i, n + 2);
+                    p0 = node_f64<KIND>(seed, s, i, n - 1, period);
+                    p1 = node_f64<KIND>(seed, s, i, n, period);
+                    p2 = node_f64<KIND>(seed, s, i, n + 1, period);
+                    p3 = node_f64<KIND>(seed, s, i, n + 2, period);
                 }
                 st.ncache[p] = n;
                 st.c[0][p] = p0;
@@ -117,7 +119,7 @@ __device__ __forceinline__ void f64_step_body(const F64Launch& a)
         const double u = a.u_in[p];
         const double ul = a.u_in[ch.offset + (i == 0 ? L - 1 : i - 1)];
         const double ur = a.u_in[ch.offset + (i + 1 == L ? 0 : i + 1)];
-        const double F = pinning_f64<KIND>(u, p, i, ch.s, a.seed, a.st);
+        const double F = pinning_f64<KIND>(u, p, i, ch.s, a.seed, a.st, ch.period);
         const double lap = __dsub_rn(__dadd_rn(ur, ul), __dmul_rn(2.0, u));
         a.u_out[p] = __dadd_rn(u, __dmul_rn(a.dt, __dadd_rn(__dadd_rn(lap, ch.f64), F)));
     }
@@ -138,7 +140,7 @@ __device__ __forceinline__ void f64_observe_body(const F64Launch& a, double (*re
             break;
         const int64_t p = ch.offset + i;
         const double u = a.u_in[p];
-        tF = __dadd_rn(tF, pinning_f64<KIND>(u, p, i, ch.s, a.seed, a.st));
+        tF = __dadd_rn(tF, pinning_f64<KIND>(u, p, i, ch.s, a.seed, a.st, ch.period));
         const double y = __dsub_rn(u, c);
         t1 = __dadd_rn(t1, y);
         t2 = __dadd_rn(t2, __dmul_rn(y, y));
@@ -184,18 +186,19 @@ __global__ void f64_init_kernel(const ChainDesc* chains, const TileDesc* tiles, 
         st.u[p] = u;
         const int32_t n = static_cast<int32_t>(floor(u));
         st.ncache[p] = n;
+        const int32_t M = ch.period;
         if (ch.kind == kRF) {
-            st.c[0][p] = rf_f64(seed, ch.s, i, n);
-            st.c[1][p] = rf_f64(seed, ch.s, i, n + 1);
+            st.c[0][p] = rf_f64(seed, ch.s, i, wrap_node(n, M));
+            st.c[1][p] = rf_f64(seed, ch.s, i, wrap_node(n + 1, M));
         } else if (ch.kind == kRBGLinear) {
-            st.c[0][p] = rbg_f64(seed, ch.s, i, n);
-            st.c[1][p] = rbg_f64(seed, ch.s, i, n + 1);
+            st.c[0][p] = rbg_f64(seed, ch.s, i, wrap_node(n, M));
+            st.c[1][p] = rbg_f64(seed, ch.s, i, wrap_node(n + 1, M));
         } else if (ch.kind == kRB) {
             for (int c = 0; c < 4; ++c)
-                st.c[c][p] = rb_f64(seed, ch.s, i, n - 1 + c);
+                st.c[c][p] = rb_f64(seed, ch.s, i, wrap_node(n - 1 + c, M));
         } else if (ch.kind == kRBGCubic) {
             for (int c = 0; c < 4; ++c)
-                st.c[c][p] = rbg_f64(seed, ch.s, i, n - 1 + c);
+                st.c[c][p] = rbg_f64(seed, ch.s, i, wrap_node(n - 1 + c, M));
         }
     }
 }

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     const float f = ch.f32;
     const float dt = a.dt;
     const uint32_t s = ch.s;
+    const int32_t M = ch.period;
 
     // ---- stage the window in this warp's shared-memory slice ----
     // Contiguous, 16-byte aligned windows arrive by TMA bulk copies (one per array, completion
@@ -276,7 +277,8 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                         const int32_t i = site_index(wstart, x, contiguous, L);
                         if constexpr (pair_kind(KIND)) {
                             // one new node: n+1 after an up move, n otherwise
-                            const float v = pair_node_f32<KIND>(a.keys, s, i, code == kMoveUp ? nn + 1 : nn, f);
+                            const float v =
+                                pair_node_f32<KIND>(a.keys, s, i, wrap_node(code == kMoveUp ? nn + 1 : nn, M), f);
                             const float2 o = s_rf[x];
                             float2 q;
                             if (code == kMoveUp)
@@ -284,11 +286,12 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                             else if (code == kMoveDown)
                                 q = make_float2(v, o.x);
                             else
-                                q = make_float2(v, pair_node_f32<KIND>(a.keys, s, i, nn + 1, f));
+                                q = make_float2(v, pair_node_f32<KIND>(a.keys, s, i, wrap_node(nn + 1, M), f));
                             s_rf[x] = q;
                         } else {
                             // one new node: n+2 after an up move, n-1 otherwise
-                            const float v = quad_node_f32<KIND>(a.keys, s, i, code == kMoveUp ? nn + 2 : nn - 1);
+                            const float v =
+                                quad_node_f32<KIND>(a.keys, s, i, wrap_node(code == kMoveUp ? nn + 2 : nn - 1, M));
                             const float4 o = s_rb[x];
                             float4 p;
                             if (code == kMoveUp)
@@ -296,9 +299,9 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                             else if (code == kMoveDown)
                                 p = make_float4(v, o.x, o.y, o.z);
                             else
-                                p = make_float4(v, quad_node_f32<KIND>(a.keys, s, i, nn),
-                                                quad_node_f32<KIND>(a.keys, s, i, nn + 1),
-                                                quad_node_f32<KIND>(a.keys, s, i, nn + 2));
+                                p = make_float4(v, quad_node_f32<KIND>(a.keys, s, i, wrap_node(nn, M)),
+                                                quad_node_f32<KIND>(a.keys, s, i, wrap_node(nn + 1, M)),
+                                                quad_node_f32<KIND>(a.keys, s, i, wrap_node(nn + 2, M)));
                             s_rb[x] = p;
                             float A, B, C;
                             rb_coefficients(p.x, p.y, p.z, p.w, f, A, B, C);
@@ -450,16 +453,18 @@ __global__ void split_init_kernel(const ChainDesc* chains, const TileDesc* tiles
         }
         st.cell[p] = n;
         st.off[p] = d;
+        const int32_t M = ch.period;
+        const int32_t m0 = wrap_node(n - 1, M), m1 = wrap_node(n, M), m2 = wrap_node(n + 1, M), m3 = wrap_node(n + 2, M);
         if (ch.kind == kRF)
-            st.rf[p] = make_float2(rf_plus_f32(seed, ch.s, i, n, ch.f32), rf_plus_f32(seed, ch.s, i, n + 1, ch.f32));
+            st.rf[p] = make_float2(rf_plus_f32(seed, ch.s, i, m1, ch.f32), rf_plus_f32(seed, ch.s, i, m2, ch.f32));
         else if (ch.kind == kRBGLinear)
-            st.rf[p] = make_float2(rbg_f32(seed, ch.s, i, n), rbg_f32(seed, ch.s, i, n + 1));
+            st.rf[p] = make_float2(rbg_f32(seed, ch.s, i, m1), rbg_f32(seed, ch.s, i, m2));
         else if (ch.kind == kRB)
-            st.rb[p] = make_float4(rb_f32(seed, ch.s, i, n - 1), rb_f32(seed, ch.s, i, n), rb_f32(seed, ch.s, i, n + 1),
-                                   rb_f32(seed, ch.s, i, n + 2));
+            st.rb[p] = make_float4(rb_f32(seed, ch.s, i, m0), rb_f32(seed, ch.s, i, m1), rb_f32(seed, ch.s, i, m2),
+                                   rb_f32(seed, ch.s, i, m3));
         else if (ch.kind == kRBGCubic)
-            st.rb[p] = make_float4(rbg_f32(seed, ch.s, i, n - 1), rbg_f32(seed, ch.s, i, n),
-                                   rbg_f32(seed, ch.s, i, n + 1), rbg_f32(seed, ch.s, i, n + 2));
+            st.rb[p] = make_float4(rbg_f32(seed, ch.s, i, m0), rbg_f32(seed, ch.s, i, m1),
+                                   rbg_f32(seed, ch.s, i, m2), rbg_f32(seed, ch.s, i, m3));
     }
 }
 

@@ -79,6 +79,10 @@ class Relaxation:
         self._check(self._lib.qew_set_precision(self._h, precision))
         self.precision = precision
 
+    def set_disorder_period(self, period: int) -> None:
+        """Disorder periodic in u with ``period`` (0: aperiodic); resets to the flat start."""
+        self._check(self._lib.qew_set_disorder_period(self._h, int(period)))
+
     def set_tuning(self, tile_w: int = 0, K: int = 0, tiles_per_cta: int = 0) -> None:
         self._check(self._lib.qew_set_tuning(self._h, tile_w, K, tiles_per_cta))
 

@@ -1,0 +1,87 @@
+"""GPU parity of the periodic disorder (the L x M samples of Sec. III.B of arXiv:1211.7275): node
+index n keys the generator as n mod M.
+
+  - both GPU paths against the oracle with the same period, per site (FP64 to 1e-12 over 10^3
+    steps; FP32-split to 1e-4, over 10^3 steps for the continuous forces and 100 steps for Cases
+    1 and 3, as for the aperiodic disorder);
+  - the split path commutes with a shift by M bit for bit: the cells move by M and every offset,
+    cache value and force is the same;
+  - period 0 is the aperiodic disorder.
+"""
+import numpy as np
+import pytest
+
+from qew_workloads import SEED, random_state
+
+pytestmark = pytest.mark.gpu
+
+RF, RB, NONE, RBG_LINEAR, RBG_CUBIC = 0, 1, 2, 3, 4
+FP32, FP64 = 0, 1
+FMOVE = {RF: 1.2, RB: 2.2, RBG_LINEAR: 2.2, RBG_CUBIC: 2.6}
+
+
+@pytest.fixture(scope="module")
+def qew():
+    import paper_1211_7275_gb300 as q
+    q.load()
+    return q
+
+
+def _run(qew, L, f, kind, steps, precision, period, u0=None, batch=2):
+    with qew.Relaxation(L, f, kind, dt=0.1, seed=SEED, precision=precision, batch=batch) as r:
+        r.set_disorder_period(period)
+        if u0 is not None:
+            r.set_state(u0)
+        obs = r.observe(steps)
+        u, _ = r.state()
+    return obs, u
+
+
+@pytest.mark.parametrize("kind", [RF, RB, RBG_LINEAR, RBG_CUBIC])
+@pytest.mark.parametrize("M", [1, 5, 37])
+def test_fp64_per_site(qew, orc, kind, M):
+    L, steps = 777, np.array([0, 1, 100, 1000])
+    obs, u = _run(qew, L, FMOVE[kind], kind, steps, FP64, M)
+    ref = orc.run([L] * 2, FMOVE[kind], 0.1, kind, SEED, steps, want_state=True, period=M)
+    assert np.max(np.abs(u - ref["u"]) / np.maximum(1.0, np.abs(ref["u"]))) <= 1e-12
+    np.testing.assert_allclose(obs["v"], ref["v"], rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("kind,n", [(RF, 1000), (RB, 1000), (RBG_LINEAR, 100), (RBG_CUBIC, 100)])
+@pytest.mark.parametrize("M", [3, 8])
+def test_split_per_site(qew, orc, kind, n, M):
+    L, steps = 1500, np.array([0, 7, n])
+    _, u = _run(qew, L, FMOVE[kind], kind, steps, FP32, M)
+    ref = orc.run([L] * 2, FMOVE[kind], 0.1, kind, SEED, steps, want_state=True, period=M)
+    assert np.max(np.abs(u - ref["u"])) <= 1e-4
+
+
+@pytest.mark.parametrize("kind", [RF, RB, RBG_LINEAR, RBG_CUBIC])
+def test_split_commutes_with_a_shift_by_the_period(qew, kind):
+    L, M, steps = 2000, 6, np.array([0, 50, 700])
+    u0 = np.round(random_state(2 * L, 0.6, seed=kind) * 64) / 64 + 3.0   # exact in FP32-split
+    _, a = _run(qew, L, FMOVE[kind], kind, steps, FP32, M, u0=u0)
+    _, b = _run(qew, L, FMOVE[kind], kind, steps, FP32, M, u0=u0 + M)
+    np.testing.assert_array_equal(b - M, a)
+
+
+def test_period_zero_is_aperiodic(qew):
+    L, steps = 1024, np.array([0, 300])
+    with qew.Relaxation(L, 1.0, RF, dt=0.1, seed=SEED, batch=2) as r:
+        r.set_disorder_period(5)
+        r.observe(steps)
+        r.set_disorder_period(0)
+        r.observe(steps)
+        u, _ = r.state()
+    with qew.Relaxation(L, 1.0, RF, dt=0.1, seed=SEED, batch=2) as r:
+        r.observe(steps)
+        u0, _ = r.state()
+    np.testing.assert_array_equal(u, u0)
+
+
+def test_bad_period(qew):
+    with qew.Relaxation(100, 1.0, RF) as r:
+        for bad in (-1, 1 << 31):
+            with pytest.raises(qew.QewError) as e:
+                r.set_disorder_period(bad)
+            assert e.value.code == -1
