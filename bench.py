@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="rf_4x2^25", choices=["rf_4x2^25", "rf_16x2^20", "rb_1024x2^16",
                                                                 "rbg_linear_4x2^25", "none_16x2^20",
-                                                                "tiny_rf_1x1024"])
+                                                                "uneven_256", "tiny_rf_1x1024"])
     p.add_argument("--relax-steps", type=int, default=4096)
     p.add_argument("--n-obs", type=int, default=12)
     p.add_argument("--tuning", default="auto", help="'auto' or tile_w,K,tiles_per_cta")
@@ -71,9 +71,31 @@ def rank_seed(rank: int) -> int:
 
 
 def workload(name: str, rank: int):
+    """Chains of a preset: L, kind, f (scalars with ``batch`` chains, or per-chain arrays with
+    batch None), the chain count, and the chain the CPU sample relaxes (``cpu``)."""
     p = W.PRESETS[name]
+    if name == "uneven_256":
+        n = p["n_chains"]
+        L = W.uneven_lengths(n)
+        kind = W.uneven_kinds(n)
+        base = np.where(kind == W.RF, W.preset_f("rf_16x2^20"), W.preset_f("rb_1024x2^16"))
+        f = base * (1.0 + W.sweep_offsets(n))
+        c = int(np.argmax(L))
+        return dict(name=name, L=L, batch=None, kind=kind, f=f, dt=p["dt"], seed=rank_seed(rank), n_chains=n,
+                    cpu=dict(L=int(L[c]), batch=1, kind=int(kind[c]), f=float(f[c]), chain=c))
     return dict(name=name, L=p["L"], batch=p["batch"], kind=p["kind"], f=W.preset_f(name), dt=p["dt"],
-                seed=rank_seed(rank))
+                seed=rank_seed(rank), n_chains=p["batch"],
+                cpu=dict(L=p["L"], batch=p["batch"], kind=p["kind"], f=W.preset_f(name), chain=0))
+
+
+def describe(wl: dict) -> dict:
+    """JSON-friendly shape of a workload."""
+    if wl["batch"] is None:
+        L = np.asarray(wl["L"])
+        return {"L": f"{wl['n_chains']} chains, L from {int(L.min())} to {int(L.max())}, {int(L.sum())} sites",
+                "kind": "mixed " + "/".join(str(k) for k in sorted(set(np.asarray(wl['kind']).tolist()))),
+                "f": "per chain (f_c^L of its kind x (1 + {-2,-1,0,1,2}%))"}
+    return {"L": wl["L"], "kind": wl["kind"], "f": wl["f"]}
 
 
 def max_over_ranks(ms: float, dist, device) -> float:
@@ -200,13 +222,14 @@ def oracle_sample(wl: dict, w: int, n_steps: int) -> dict:
     import oracle
     oracle.build()
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
-    L = wl["L"]
-    jobs = [(t % wl["batch"], (t * w * 7919) % L) for t in range(cores)]
+    cs = wl["cpu"]
+    L = cs["L"]
+    jobs = [(cs["chain"] if wl["batch"] is None else t % cs["batch"], (t * w * 7919) % L) for t in range(cores)]
     errs = []
 
     def work(c, i0):
         try:
-            oracle.lightcone(L, c, wl["f"], wl["dt"], wl["kind"], wl["seed"], i0, w, n_steps)
+            oracle.lightcone(L, c, cs["f"], wl["dt"], cs["kind"], wl["seed"], i0, w, min(n_steps, (L - w) // 2))
         except Exception as e:  # pragma: no cover
             errs.append(e)
 
@@ -219,9 +242,10 @@ def oracle_sample(wl: dict, w: int, n_steps: int) -> dict:
     dt = time.perf_counter() - t0
     if errs:
         raise errs[0]
-    updates = cores * w * n_steps
+    n_eff = min(n_steps, (L - w) // 2)
+    updates = cores * w * n_eff
     return {"value": updates / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{cores} threads x one light-cone window of {w} sites x {n_steps} Euler steps of the "
+            "sample": f"{cores} threads x one light-cone window of {w} sites x {n_eff} Euler steps of the "
                       f"{wl['name']} chains (exact sites of the full-size chains), {dt:.1f} s",
             "seconds": dt}
 
@@ -230,7 +254,7 @@ def run_reference(args, rank: int, world: int) -> None:
     if rank != 0:
         return
     wl = workload(args.workload, 0)
-    w, n = 1 << 20, 48
+    w, n = min(1 << 20, wl["cpu"]["L"] // 2), 48
     for _ in range(args.warmup):
         oracle_sample(wl, w, n)
     vals, secs = [], []
@@ -246,7 +270,7 @@ def run_reference(args, rank: int, world: int) -> None:
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": wl["name"], "L": wl["L"], "batch": wl["batch"], "kind": wl["kind"], "f": wl["f"],
+        "config": {"workload": wl["name"], **describe(wl), "batch": wl["n_chains"],
                    "dt": wl["dt"], "arm": "CPU FP64 oracle (plain C, one light-cone window per host thread)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": r["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -326,12 +350,15 @@ def main() -> None:
     per_launch_ms = st["fused_ms"] / max(1, st["fused_launches"])
     su_per_launch = st["site_updates"] / max(1, st["fused_launches"])
     r_cross = st["crossings"] / max(1, st["site_updates"])
-    kind = wl["kind"]
-    ops_per_su = OPS_BASE[kind] + OPS_PER_CROSSING[kind] * r_cross
+    # per-kind figures weighted by the sites of each kind (one kind for every preset but the mixed batch)
+    kinds = np.broadcast_to(np.asarray(wl["kind"]), (wl["n_chains"],))
+    sites = np.broadcast_to(np.asarray(wl["L"], dtype=np.float64), (wl["n_chains"],))
+    wk = {int(k): float(sites[kinds == k].sum() / sites.sum()) for k in set(kinds.tolist())}
+    ops_per_su = sum(w * (OPS_BASE[k] + OPS_PER_CROSSING[k] * r_cross) for k, w in wk.items())
     achieved = ops_per_su * su_per_launch / (per_launch_ms / 1e3) / 1e12
     peak = sms * LANES_PER_SM * clk * 1e6 / 1e12
     tile_w, K, tpc = tuning
-    bytes_per_su = 2 * (8 + 4 * (4 if kind in QUAD_KINDS else 2 if kind != 2 else 0)) / K   # state + cache, r+w per K steps
+    bytes_per_su = sum(w * 2 * (8 + 4 * (4 if k in QUAD_KINDS else 2 if k != 2 else 0)) for k, w in wk.items()) / K
     hbm_achieved = bytes_per_su * su_per_launch / (per_launch_ms / 1e3) / 1e9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     traffic = profiled_traffic()
@@ -352,7 +379,7 @@ def main() -> None:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         S = relax.structure_factor()
-        sq = {"ms": 1e3 * (time.perf_counter() - t0), "modes": int(S.size), "chains": int(wl["batch"]),
+        sq = {"ms": 1e3 * (time.perf_counter() - t0), "modes": int(S.size), "chains": int(wl["n_chains"]),
               "includes": "state to FP64 rows, batched real-to-complex cuFFT, mean |u_q|^2 over chains, "
                           "copy to host (work area allocated and freed in the call)"}
 
@@ -399,8 +426,8 @@ def main() -> None:
             r.close()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        h2d = sched.nbytes + wl["batch"] * (8 + 8 + 4)
-        d2h = len(sched) * wl["batch"] * 4 * 8
+        h2d = sched.nbytes + wl["n_chains"] * (8 + 8 + 4)
+        d2h = len(sched) * wl["n_chains"] * 4 * 8
         e2e = {"value": n_sites * args.relax_steps * n_e2e / wall, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": n_e2e,
                "includes": "handle creation (device allocation + flat-start init), relaxation with fused "
@@ -412,16 +439,18 @@ def main() -> None:
         cpu = oracle_sample(wl, 1 << 20, 128)
         cpu.pop("seconds", None)
 
+    state_gib = sum(w * (8 + 4 * (4 if k in QUAD_KINDS else 2 if k != 2 else 0)) for k, w in wk.items()) * n_sites / 2 ** 30
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl["name"], "L": wl["L"], "batch_per_gpu": wl["batch"], "kind": kind,
-                       "f": wl["f"], "dt": wl["dt"], "relax_steps": args.relax_steps,
+            "config": {"workload": wl["name"], **describe(wl), "batch_per_gpu": wl["n_chains"],
+                       "dt": wl["dt"], "relax_steps": args.relax_steps,
                        "observations": int(len(sched)), "precision": "int32 cell + f32 offset, f64 reductions",
                        "tuning": {"tile_w": tile_w, "K": K, "tiles_per_cta": tpc},
-                       "l2": "inputs larger than L2 (4 GiB state), no flush",
+                       "l2": (f"inputs larger than L2 ({state_gib:.2f} GiB state), no flush" if state_gib > 0.129
+                              else f"state of {state_gib * 1024:.1f} MiB fits in L2 (not a bandwidth measurement)"),
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "roofline": roofline, "fp64_path": fp64, "cpu_baseline": cpu, "e2e": e2e, "structure_factor": sq,
             "gpu_launches": st["launches"], "clocks": clocks,
