@@ -23,6 +23,8 @@ Functions and the passages they follow:
                      w central sites after n steps (stencil radius 1).
   structure_factor   S_q of Eq. 6 (Sec. II): the sample mean of |(1/L) sum_x u(x) e^{-iqx}|^2
                      at q = 2 pi n / L, n = 1 .. L/2, by a real FFT of each chain.
+  critical_force     f_c^s of a periodic L x M sample (Sec. III.B): the largest drive with a
+                     pinned configuration in the long-time dynamics, by bisection on f.
 
 Parity of every function is pinned by ``tests/test_oracle_*.py``.
 """
@@ -192,3 +194,47 @@ def structure_factor(u, L: int, n_modes: int | None = None) -> np.ndarray:
         raise ValueError("n_modes must lie in [1, L/2]")
     z = np.fft.rfft(u, axis=1)[:, 1:m + 1] / L
     return np.mean(z.real ** 2 + z.imag ** 2, axis=0)
+
+
+def critical_force(L: int, M: int, kind: int, seed: int, s: int = 0, *, f_hi: float = 3.0, tol: float = 1e-4,
+                   dt: float = 0.1, chunk: int = 2000, max_steps: int = 1_000_000, v_tol: float = 1e-12,
+                   f_start: float = 0.0) -> dict:
+    """Critical force f_c^s and critical configuration of the periodic L x M sample ``s`` (Sec. III.B:
+    the pinned configuration with the largest drive in the long-time dynamics), by bisection on f.
+
+    A trial force f starts from the pinned configuration u_lo of the largest force f_lo known to
+    pin.  There every velocity equals f - f_lo > 0, and the Euler map keeps the order of
+    configurations (Middleton's no-passing), so the line only moves forward.  It either
+      - pins: the mean velocity falls below ``v_tol``; f <= f_c^s and the pinned state becomes
+        u_lo; or
+      - runs away: every site passes u_lo + M.  The disorder repeats with period M, so from there
+        the line repeats its motion one period higher, forever: no pinned configuration exists,
+        and f > f_c^s.
+    The first u_lo is the state the line relaxes to at f = f_start (below f_c^s) from the flat
+    start.  Returns f_c^s (the bracket's midpoint), the bracket and the critical configuration u_lo.
+    """
+    def relax(f: float, u0: np.ndarray):
+        u, t = u0.copy(), 0
+        while t < max_steps:
+            r = run([L], f, dt, kind, seed, [0, chunk], s=[s], u0=u, want_state=True, period=M)
+            u, t = r["u"], t + chunk
+            if np.min(u - u0) >= M:
+                return "moving", u
+            if abs(r["v"][-1, 0]) < v_tol:
+                return "pinned", u
+        return "undecided", u
+
+    state, u_lo = relax(f_start, np.zeros(L))
+    if state != "pinned":
+        raise RuntimeError(f"the flat line does not pin at f = {f_start} ({state})")
+    lo, hi = float(f_start), float(f_hi)
+    while hi - lo > tol:
+        mid = 0.5 * (lo + hi)
+        state, u = relax(mid, u_lo)
+        if state == "moving":
+            hi = mid
+        elif state == "pinned":
+            lo, u_lo = mid, u
+        else:
+            raise RuntimeError(f"no decision at f = {mid} within {max_steps} steps")
+    return {"f_c": 0.5 * (lo + hi), "bracket": [lo, hi], "u_c": u_lo}
