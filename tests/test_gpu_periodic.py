@@ -85,3 +85,36 @@ def test_bad_period(qew):
             with pytest.raises(qew.QewError) as e:
                 r.set_disorder_period(bad)
             assert e.value.code == -1
+
+
+def test_critical_force_matches_oracle(qew, orc):
+    """f_c^s of periodic 64 x 64 random-field samples (Sec. III.B), bisected on the GPU's FP64 path
+    and on the oracle: the two dynamics agree to rounding, so every trial takes the same decision
+    and the brackets are equal."""
+    from paper_1211_7275_gb300 import critical
+    res = critical.critical_forces(64, 64, RF, 4, seed=SEED, tol=1e-4)
+    for s in range(4):
+        ref = orc.critical_force(64, 64, RF, SEED, s, tol=1e-4)
+        assert res["lo"][s] == ref["bracket"][0] and res["hi"][s] == ref["bracket"][1], (s, res["f_c"][s], ref["f_c"])
+        assert np.max(np.abs(res["u_c"][s] - ref["u_c"])) <= 1e-9
+
+
+def test_critical_force_single_site_closed_form(qew, orc):
+    from paper_1211_7275_gb300 import critical
+    M = 16
+    res = critical.critical_forces(1, M, RF, 6, seed=SEED, tol=1e-5)
+    for s in range(6):
+        R = orc.disorder_values(RF, SEED, s, np.zeros(M, np.int64), np.arange(M))
+        assert res["lo"][s] <= -R.min() <= res["hi"][s]
+
+
+def test_critical_force_mean_near_the_short_time_threshold(qew):
+    """Sec. IV.A: the thermodynamic f_c of the critical configurations is the threshold of the
+    short-time dynamics.  8 random-field samples of 512 x 512: the mean f_c^s within 5% of the
+    GPU-bisected STD threshold of the 16 x 2^20 preset."""
+    from paper_1211_7275_gb300 import critical
+    from qew_workloads import preset_f
+    res = critical.critical_forces(512, 512, RF, 8, seed=SEED, tol=1e-3)
+    fc_std = preset_f("rf_16x2^20")
+    print(f"mean f_c^s (512 x 512, 8 samples) = {np.mean(res['f_c']):.4f}, STD f_c^L = {fc_std:.4f}")
+    assert abs(np.mean(res["f_c"]) - fc_std) < 0.05 * fc_std
