@@ -305,7 +305,9 @@ def main() -> None:
 
     wl = workload(args.workload, rank)
     sched = W.log_spaced_steps(args.relax_steps, args.n_obs)
-    stream = torch.cuda.current_stream()
+    # A stream of its own (torch's default stream has the null handle, which the library reads as
+    # "use your own stream"): the kernels and the timing events then share one stream.
+    stream = torch.cuda.Stream(device=local)
     relax = q.Relaxation(wl["L"], wl["f"], wl["kind"], dt=wl["dt"], seed=wl["seed"], precision=q.FP32_SPLIT,
                          batch=wl["batch"], stream=stream)
     if args.tuning == "auto":

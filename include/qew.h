@@ -116,9 +116,9 @@ int qew_set_disorder_period(qew_handle h, int64_t period);
  * `K` Euler steps per HBM round trip (temporal-block depth, 1 <= K <= tile_w / 4),
  * `tiles_per_cta` warp tiles per thread block (1, 2, 4 or 8).
  * Passing 0 for all three asks for the autotuner: it times candidate shapes on the handle's own
- * chains, without changing their state, as soon as they are at least 256 Euler steps past the
- * flat start (the first steps, where every site starts to move at once, are not
- * representative); until then the default shape is used.
+ * chains, without changing their state, as soon as they are at least 1024 Euler steps past the
+ * flat start (the best shape changes while the rate of cell crossings decays after the flat
+ * start); until then the default shape is used.
  * Results never depend on the shape beyond FP32 rounding order, which is identical: each
  * site's arithmetic is the same for every shape.
  */

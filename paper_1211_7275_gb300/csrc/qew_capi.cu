@@ -451,8 +451,11 @@ F64Launch f64_args(qew_ctx* h)
 int autotune(qew_ctx* h);
 
 // The autotuner times candidate shapes only once the chains are this many steps past the flat
-// start: the first steps (every site starting to move at once) are not representative.
-constexpr int64_t kTuneAfterSteps = 256;
+// start.  The best shape changes while the crossing rate decays: measured on 4 x 2^25 random-
+// field chains at f_c, 736-site tiles are 4% faster than 992-site ones over steps 0-256, equal
+// over 256-768, and 6% slower after step 2048 (the larger tiles fill their regeneration rounds
+// better).  Step 1024 is past the crossover.
+constexpr int64_t kTuneAfterSteps = 1024;
 
 // Advance to `target` (>= current step); with `obs` record the observables there into obs.
 int run_to(qew_ctx* h, int64_t target, double* obs)
@@ -549,18 +552,22 @@ int autotune(qew_ctx* h)
                 int rc = build_layout(h);
                 if (rc != QEW_OK)
                     return rc;
+                // best of four timed repetitions (after one untimed), each two launches long, so a
+                // shape wins by its throughput rather than by the noise of a single launch
                 float ms_best = 1e30f;
-                for (int rep = 0; rep < 3; ++rep) {
+                for (int rep = 0; rep < 5; ++rep) {
                     cudaEventRecord(e0, h->stream);
-                    rc = launch_split_all(h, K, 0, h->sp[h->cur], h->sp[h->cur ^ 1]);
-                    if (rc != QEW_OK)
-                        return rc;
+                    for (int l = 0; l < 2; ++l) {
+                        rc = launch_split_all(h, K, 0, h->sp[h->cur], h->sp[h->cur ^ 1]);
+                        if (rc != QEW_OK)
+                            return rc;
+                    }
                     cudaEventRecord(e1, h->stream);
                     QEW_CUDA(h, cudaEventSynchronize(e1), "timing a tuning candidate");
                     float ms = 0;
                     cudaEventElapsedTime(&ms, e0, e1);
                     if (rep > 0)
-                        ms_best = std::min(ms_best, ms);
+                        ms_best = std::min(ms_best, 0.5f * ms);
                 }
                 const float per = ms_best / static_cast<float>(K);
                 if (per < best) {
