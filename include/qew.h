@@ -112,7 +112,8 @@ int qew_set_disorder_period(qew_handle h, int64_t period);
 
 /*
  * qew_set_tuning -- launch shape of the fused FP32-split kernel: `tile_w` sites per warp tile
- * (32 lanes x an odd number of sites: 224, 480, 736 or 992; random-bond chains 224 or 480),
+ * (32 lanes x an odd number of sites: 224, 480, 736, 992 or 1248; cubic random-bond chains 224
+ * or 480, disorder-free chains up to 992),
  * `K` Euler steps per HBM round trip (temporal-block depth, 1 <= K <= tile_w / 4),
  * `tiles_per_cta` warp tiles per thread block (1, 2, 4 or 8).
  * Passing 0 for all three asks for the autotuner: it times candidate shapes on the handle's own

@@ -525,9 +525,9 @@ int autotune(qew_ctx* h)
             return build_layout(h);
         }
     }
-    const int S_all[] = {7, 15, 23, 31};
+    const int S_all[] = {7, 15, 23, 31, 39};
     const int K_all[] = {8, 16, 32};
-    const int T_all[] = {2, 4};
+    const int T_all[] = {1, 2, 4};
     float best = 1e30f;
     int bS = h->S, bK = h->K, bT = h->tpc;
     cudaEvent_t e0, e1;
@@ -998,7 +998,7 @@ int qew_set_tuning(qew_handle h, int32_t tile_w, int32_t K, int32_t tiles_per_ct
         return QEW_OK;
     }
     if (tile_w % 32 != 0)
-        return fail(h, QEW_EINVAL, "tile_w must be one of 224, 480, 736, 992");
+        return fail(h, QEW_EINVAL, "tile_w must be one of 224, 480, 736, 992, 1248");
     const int S = tile_w / 32;
     for (int k = 0; k < kNumKinds; ++k)
         if ((h->kinds_mask >> k & 1) && !split_supported(k, S))

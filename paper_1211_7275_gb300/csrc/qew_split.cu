@@ -31,6 +31,7 @@
 // written straight into the shared-memory cache of the requesting sites; the direction of each
 // move is recovered from the cell the cache was drawn for, kept per site in shared memory.
 #include <cstdio>
+#include <type_traits>
 
 #include "qew_internal.h"
 #include "qew_tma.cuh"
@@ -83,16 +84,29 @@ __device__ __forceinline__ float drive_plus_pinning(const float2* s_rf, const fl
     }
 }
 
-// Queue entry codes (bits 16..17 of the first word; bits 0..15 hold the window position).
+// Per-lane mask of the sites that moved in a step: 32 bits while a lane holds at most 32 sites,
+// 64 beyond.  The bit of site j is a compile-time constant in the unrolled update loop, so each
+// site still sets one bit of one 32-bit word.
+template <int S>
+using MoveMask = typename std::conditional<(S <= 32), unsigned, unsigned long long>::type;
+
+__device__ __forceinline__ int mask_popc(unsigned m) { return __popc(m); }
+__device__ __forceinline__ int mask_popc(unsigned long long m) { return __popcll(m); }
+__device__ __forceinline__ int mask_ffs(unsigned m) { return __ffs(m); }
+__device__ __forceinline__ int mask_ffs(unsigned long long m) { return __ffsll(static_cast<long long>(m)); }
+
+// Kinds of cell move.
 constexpr int kMoveUp = 1;
 constexpr int kMoveDown = 2;
 constexpr int kMoveFar = 3;
 
-// Resident 256-thread blocks per SM asked of the register allocator, per kind and lanes' sites:
-// the largest count for which the kernel still needs no (or almost no) register spills.
+// Resident 256-thread blocks per SM asked of the register allocator, per kind and lanes' sites.
+// For the two-node kinds at S <= 15 this keeps a few bytes of spill in the regeneration path:
+// measured on Case 3 (which regenerates often), the occupancy is worth more than the spill
+// (3.4e11 vs 3.1e11 site-updates/s with a spill-free, lower-occupancy register budget).
 template <int KIND, int S>
 struct MinBlocks {
-    static constexpr int value = (S <= 8) ? (quad_kind(KIND) ? 3 : 4) : (S <= 16) ? (quad_kind(KIND) ? 2 : 3) : 2;
+    static constexpr int value = (S <= 8) ? (quad_kind(KIND) ? 3 : 4) : (S <= 16) ? (quad_kind(KIND) ? 2 : 3) : (S <= 31) ? 2 : 1;
 };
 
 // Sites per lane are odd: lane l reads its cache at word offsets 2 S l (pair) or 4 S l (quad), and
@@ -217,7 +231,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
         const float cr = (lane == 31) ? c[S - 1] : cr0;
         const float drn = (lane == 31) ? d[S - 1] : dr0;
         float Dm = (c[0] - cl) + (d[0] - dl);   // u_j - u_{j-1}
-        unsigned mv = 0;   // sites that changed cell in this step
+        MoveMask<S> mv = 0;   // sites that changed cell in this step (bit j: the lane's site j)
 #pragma unroll
         for (int j = 0; j < S; ++j) {
             const int x = lane * S + j;
@@ -232,7 +246,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
             const float fl = floorf(dn);
             c[j] += fl;
             d[j] = dn - fl;
-            mv |= (fl != 0.0f) ? (1u << j) : 0u;
+            mv |= (fl != 0.0f) ? (MoveMask<S>(1) << j) : MoveMask<S>(0);
         }
         const unsigned anymv = __reduce_or_sync(kFull, mv);
         if (anymv) {
@@ -244,7 +258,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
             }
             // queue slots: warp prefix sum of the lanes' move counts; each lane then walks the set
             // bits of its mask.  Chunks of 32 requests, one Philox value per lane and chunk.
-            const int cnt = __popc(mv);
+            const int cnt = mask_popc(mv);
             int incl = cnt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -258,10 +272,10 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                 const int excl = incl - cnt;
                 for (int base = 0; base < qn; base += 32) {
                     int q = excl;
-                    unsigned m = mv;
-                    while (m != 0u && q < base + 32) {
-                        const int b = __ffs(m) - 1;
-                        m &= m - 1u;
+                    MoveMask<S> m = mv;
+                    while (m != 0 && q < base + 32) {
+                        const int b = mask_ffs(m) - 1;
+                        m &= m - 1;
                         if (q >= base)
                             s_q[q - base] = (lane << 8) | b;
                         ++q;
@@ -491,7 +505,9 @@ bool split_supported(int kind, int S)
 {
     if (quad_kind(kind))
         return S == 7 || S == 15;
-    return S == 7 || S == 15 || S == 23 || S == 31;
+    if (kind == kNone)
+        return S == 7 || S == 15 || S == 23 || S == 31;
+    return S == 7 || S == 15 || S == 23 || S == 31 || S == 39;
 }
 
 size_t split_smem_bytes(int kind, int S, int tiles_per_cta)
@@ -508,6 +524,7 @@ cudaError_t split_step(int kind, int S, int tiles_per_cta, const SplitLaunch& a,
         case 15: return launch_split<kRF, 15>(tiles_per_cta, a, st);
         case 23: return launch_split<kRF, 23>(tiles_per_cta, a, st);
         case 31: return launch_split<kRF, 31>(tiles_per_cta, a, st);
+        case 39: return launch_split<kRF, 39>(tiles_per_cta, a, st);
         }
     } else if (kind == kRBGLinear) {
         switch (S) {
@@ -515,6 +532,7 @@ cudaError_t split_step(int kind, int S, int tiles_per_cta, const SplitLaunch& a,
         case 15: return launch_split<kRBGLinear, 15>(tiles_per_cta, a, st);
         case 23: return launch_split<kRBGLinear, 23>(tiles_per_cta, a, st);
         case 31: return launch_split<kRBGLinear, 31>(tiles_per_cta, a, st);
+        case 39: return launch_split<kRBGLinear, 39>(tiles_per_cta, a, st);
         }
     } else if (kind == kRB) {
         switch (S) {

@@ -130,7 +130,7 @@ def test_split_case3_per_site(qew, orc, L):
 
 
 @pytest.mark.parametrize("kind,shapes", [
-    (RBG_LINEAR, [(480, 16, 4), (224, 8, 2), (992, 32, 1), (736, 24, 8), (480, 13, 2)]),
+    (RBG_LINEAR, [(480, 16, 4), (224, 8, 2), (992, 32, 1), (736, 24, 8), (480, 13, 2), (1248, 32, 1)]),
     (RBG_CUBIC, [(224, 16, 4), (480, 8, 2), (224, 13, 1), (480, 32, 8)]),
     (RB, [(224, 16, 4), (480, 8, 2), (224, 13, 1), (480, 32, 8)]),
 ])

@@ -94,7 +94,7 @@ def test_fp64_closed_form(qew):
 # ------------------------------------------------------------------------------------------
 # FP32-split fused path
 # ------------------------------------------------------------------------------------------
-SHAPES = [(480, 16, 4), (224, 8, 2), (992, 32, 1), (736, 24, 8), (480, 13, 2)]
+SHAPES = [(480, 16, 4), (224, 8, 2), (992, 32, 1), (736, 24, 8), (480, 13, 2), (1248, 32, 1), (1248, 9, 2)]
 
 
 def _split_check(u, cells, ref_u, tol=1e-4):
