@@ -112,9 +112,11 @@ int qew_set_disorder_period(qew_handle h, int64_t period);
 
 /*
  * qew_set_tuning -- launch shape of the fused FP32-split kernel: `tile_w` sites per warp tile
- * (32 lanes x an odd number of sites: 224, 480, 736, 992 or 1248; cubic random-bond chains 224
- * or 480, disorder-free chains up to 992),
- * `K` Euler steps per HBM round trip (temporal-block depth, 1 <= K <= tile_w / 4),
+ * (32 lanes x an odd number of sites: 224, 480, 736, 992 or 1248).  Each disorder kind takes the
+ * widest tile it supports up to tile_w: cubic random-bond chains (Cases 1 and 2) at most 480,
+ * disorder-free chains at most 992, so in a mixed batch every kind runs its own widest tile.
+ * `K` Euler steps per HBM round trip (temporal-block depth, 1 <= K <= w / 4 for the narrowest
+ * tile w in use),
  * `tiles_per_cta` warp tiles per thread block (1, 2, 4 or 8).
  * Passing 0 for all three asks for the autotuner: it times candidate shapes on the handle's own
  * chains, without changing their state, as soon as they are at least 1024 Euler steps past the
@@ -125,7 +127,8 @@ int qew_set_disorder_period(qew_handle h, int64_t period);
  */
 int qew_set_tuning(qew_handle h, int32_t tile_w, int32_t K, int32_t tiles_per_cta);
 
-/* qew_get_tuning -- the shape in use (after autotuning, the one it picked). */
+/* qew_get_tuning -- the shape in use (after autotuning, the one it picked); tile_w is the widest
+ * tile among the batch's kinds. */
 int qew_get_tuning(qew_handle h, int32_t* tile_w, int32_t* K, int32_t* tiles_per_cta);
 
 /* qew_advance -- n_steps >= 0 Euler steps of every chain. */

@@ -94,7 +94,7 @@ struct qew_ctx {
     TileDesc* d_tiles[kNumKinds] = {};
     int32_t n_tiles[kNumKinds] = {};
     int32_t tile_base[kNumKinds] = {};
-    int32_t w_own = 0;
+    int32_t w_own[kNumKinds] = {};   // sites a warp tile owns, per disorder kind
     TileDesc* d_btiles = nullptr;
     int32_t n_btiles = 0;
 
@@ -271,13 +271,45 @@ int alloc_state(qew_ctx* h)
     return QEW_OK;
 }
 
+// Sites per lane that chains of `kind` use under the requested S: the largest width the kind
+// supports up to S (every kind supports 7), so that in a mixed batch each kind gets its own
+// widest tile.
+int kind_S(int kind, int S)
+{
+    const int all[] = {39, 31, 23, 15, 7};
+    for (int s : all)
+        if (s <= S && split_supported(kind, s))
+            return s;
+    return 7;
+}
+
+// The narrowest tile among the kinds present: K is bounded by it.
+int min_kind_S(const qew_ctx* h, int S)
+{
+    int m = S;
+    for (int k = 0; k < kNumKinds; ++k)
+        if (h->kinds_mask >> k & 1)
+            m = std::min(m, kind_S(k, S));
+    return m;
+}
+
+// Largest shared-memory footprint among the kinds present, for S sites per lane requested.
+size_t max_kind_smem(const qew_ctx* h, int S, int tiles_per_cta)
+{
+    size_t m = 0;
+    for (int k = 0; k < kNumKinds; ++k)
+        if (h->kinds_mask >> k & 1)
+            m = std::max(m, split_smem_bytes(k, kind_S(k, S), tiles_per_cta));
+    return m;
+}
+
 // Tile lists for the current precision and launch shape; uploads chain descriptors and sizes
 // the partial-sum buffer.
 int build_layout(qew_ctx* h)
 {
     drop_graph(h);   // captured launches point at the descriptors rebuilt here
-    const int32_t tile_w = 32 * h->S;
-    h->w_own = tile_w - 2 * h->K;
+    for (int k = 0; k < kNumKinds; ++k)
+        h->w_own[k] = 32 * kind_S(k, h->S) - 2 * h->K;
     std::vector<TileDesc> lists[kNumKinds];
     std::vector<TileDesc> blocks;
     h->h_chains.assign(h->n_chains, ChainDesc{});
@@ -296,7 +328,7 @@ int build_layout(qew_ctx* h)
         if (h->precision == QEW_FP32_SPLIT) {
             auto& lst = lists[d.kind];
             first[c] = static_cast<int32_t>(lst.size());
-            for (int64_t st = 0; st < d.L; st += h->w_own)
+            for (int64_t st = 0; st < d.L; st += h->w_own[d.kind])
                 lst.push_back(TileDesc{c, static_cast<int32_t>(st)});
             count[c] = static_cast<int32_t>(lst.size()) - first[c];
         }
@@ -383,7 +415,7 @@ SplitLaunch split_args(qew_ctx* h, int kind, int K, int do_obs, SplitState in, S
     a.in = in;
     a.out = out;
     a.K = K;
-    a.w_own = h->w_own;
+    a.w_own = h->w_own[kind];
     a.dt = static_cast<float>(h->dt);
     a.seed = h->seed;
     a.do_obs = do_obs;
@@ -421,7 +453,7 @@ int launch_split_all(qew_ctx* h, int K, int do_obs, SplitState in, SplitState ou
                 return rc;
             QEW_CUDA(h, cudaEventRecord(e0, h->stream), "recording a timing event");
         }
-        QEW_CUDA(h, split_step(k, h->S, h->tpc, a, h->stream), "launching the fused step kernel");
+        QEW_CUDA(h, split_step(k, kind_S(k, h->S), h->tpc, a, h->stream), "launching the fused step kernel");
         if (h->stats_on)
             QEW_CUDA(h, cudaEventRecord(e1, h->stream), "recording a timing event");
         h->n_launches += 1;
@@ -534,17 +566,18 @@ int autotune(qew_ctx* h)
     QEW_CUDA(h, cudaEventCreate(&e0), "creating tuning events");
     QEW_CUDA(h, cudaEventCreate(&e1), "creating tuning events");
     for (int S : S_all) {
-        bool ok = true;
+        // a requested width that no kind present runs would repeat a narrower candidate
+        bool used = false;
         for (int k = 0; k < kNumKinds; ++k)
-            if ((h->kinds_mask >> k & 1) && !split_supported(k, S))
-                ok = false;
-        if (!ok)
+            if ((h->kinds_mask >> k & 1) && kind_S(k, S) == S)
+                used = true;
+        if (!used)
             continue;
         for (int K : K_all) {
-            if (4 * K > 32 * S)
+            if (4 * K > 32 * min_kind_S(h, S))
                 continue;
             for (int T : T_all) {
-                if (split_smem_bytes((h->kinds_mask & kQuadMask) ? kRB : kRF, S, T) > 200 * 1024)
+                if (max_kind_smem(h, S, T) > 200 * 1024)
                     continue;
                 h->S = S;
                 h->K = K;
@@ -1000,14 +1033,13 @@ int qew_set_tuning(qew_handle h, int32_t tile_w, int32_t K, int32_t tiles_per_ct
     if (tile_w % 32 != 0)
         return fail(h, QEW_EINVAL, "tile_w must be one of 224, 480, 736, 992, 1248");
     const int S = tile_w / 32;
-    for (int k = 0; k < kNumKinds; ++k)
-        if ((h->kinds_mask >> k & 1) && !split_supported(k, S))
-            return fail(h, QEW_EINVAL, "tile_w " + std::to_string(tile_w) + " is not supported for this disorder kind");
-    if (K < 1 || 4 * K > tile_w)
-        return fail(h, QEW_EINVAL, "K must lie in [1, tile_w / 4]");
+    if (S != 7 && S != 15 && S != 23 && S != 31 && S != 39)
+        return fail(h, QEW_EINVAL, "tile_w must be one of 224, 480, 736, 992, 1248");
+    if (K < 1 || 4 * K > 32 * min_kind_S(h, S))
+        return fail(h, QEW_EINVAL, "K must lie in [1, tile_w / 4] for the narrowest tile in use");
     if (tiles_per_cta != 1 && tiles_per_cta != 2 && tiles_per_cta != 4 && tiles_per_cta != 8)
         return fail(h, QEW_EINVAL, "tiles_per_cta must be 1, 2, 4 or 8");
-    if (split_smem_bytes((h->kinds_mask & kQuadMask) ? kRB : kRF, S, tiles_per_cta) > 227 * 1024)
+    if (max_kind_smem(h, S, tiles_per_cta) > 227 * 1024)
         return fail(h, QEW_EINVAL, "tile_w * tiles_per_cta needs more shared memory than a block has");
     h->S = S;
     h->K = K;
@@ -1020,8 +1052,13 @@ int qew_get_tuning(qew_handle h, int32_t* tile_w, int32_t* K, int32_t* tiles_per
 {
     if (int rc = check_handle(h))
         return rc;
-    if (tile_w)
-        *tile_w = 32 * h->S;
+    if (tile_w) {
+        int S = 7;
+        for (int k = 0; k < kNumKinds; ++k)
+            if (h->kinds_mask >> k & 1)
+                S = std::max(S, kind_S(k, h->S));
+        *tile_w = 32 * S;
+    }
     if (K)
         *K = h->K;
     if (tiles_per_cta)

@@ -171,6 +171,28 @@ def test_mixed_batch_all_kinds(qew, orc):
         np.testing.assert_allclose(obs["w2"], ref["w2"], rtol=2e-3, atol=1e-5)
 
 
+def test_mixed_batch_per_kind_tile_widths(qew):
+    """In a mixed batch each kind runs the widest tile it supports up to the requested one (cubic
+    random-bond chains at most 480 sites, disorder-free chains at most 992): the states agree bit
+    for bit with those of the narrowest common shape, and the reported width is the widest in use."""
+    L = np.array([3000, 4097, 777, 5025, 2048, 9999])
+    kind = np.array([RF, RB, NONE, RBG_LINEAR, RBG_CUBIC, RF], dtype=np.int32)
+    f = np.array([1.0, 1.9, 0.5, 2.2, 2.6, 1.2])
+    steps = np.array([0, 5, 333, 600])
+    runs = []
+    for shape, want_w in [((224, 8, 2), 224), ((1248, 32, 1), 1248), ((992, 16, 2), 992), ((736, 24, 4), 736)]:
+        with qew.Relaxation(L, f, kind, dt=0.1, seed=SEED) as r:
+            r.set_tuning(*shape)
+            assert r.tuning()[0] == want_w
+            r.observe(steps)
+            runs.append((r.state()[0], r.cells()))
+    for u, c in runs[1:]:
+        assert np.array_equal(u, runs[0][0]) and np.array_equal(c, runs[0][1])
+    with qew.Relaxation(L[1:2], f[1:2], kind[1:2], dt=0.1, seed=SEED) as r:
+        r.set_tuning(1248, 32, 1)   # a cubic random-bond batch alone: 480-site tiles
+        assert r.tuning()[0] == 480
+
+
 @pytest.mark.parametrize("precision", [FP32, FP64])
 def test_case3_mean_velocity_invariant(qew, precision):
     """dubar = dt v also with the discontinuous force: the periodic Laplacian sums to zero."""
