@@ -101,9 +101,9 @@ constexpr int kMoveDown = 2;
 constexpr int kMoveFar = 3;
 
 // Resident 256-thread blocks per SM asked of the register allocator, per kind and lanes' sites.
-// For the two-node kinds at S <= 15 this keeps a few bytes of spill in the regeneration path:
-// measured on Case 3 (which regenerates often), the occupancy is worth more than the spill
-// (3.4e11 vs 3.1e11 site-updates/s with a spill-free, lower-occupancy register budget).
+// Measured: on Case 3 (which regenerates often) a lower-occupancy budget lost 10%, and on the
+// random field at S = 31 the 144 registers the allocator takes unasked lost 3% against the
+// 128 asked here.
 template <int KIND, int S>
 struct MinBlocks {
     static constexpr int value = (S <= 8) ? (quad_kind(KIND) ? 3 : 4) : (S <= 16) ? (quad_kind(KIND) ? 2 : 3) : (S <= 31) ? 2 : 1;
@@ -289,8 +289,26 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                         s_ccell[x] = nn;
                         const int code = (nn == prev + 1) ? kMoveUp : (nn == prev - 1) ? kMoveDown : kMoveFar;
                         const int32_t i = site_index(wstart, x, contiguous, L);
-                        if constexpr (pair_kind(KIND)) {
-                            // one new node: n+1 after an up move, n otherwise
+                        if constexpr (pair_kind(KIND) && S < 31) {
+                            // one new node, n+1 after an up move and n after a down move; a far move
+                            // draws n and n+1.  One call site, with a second trip only for far moves:
+                            // a second inlined transform would spill registers at S <= 15.
+                            const float2 o = s_rf[x];
+                            float2 q = (code == kMoveUp) ? make_float2(o.y, 0.0f) : make_float2(0.0f, o.x);
+                            const int n0 = (code == kMoveUp) ? nn + 1 : nn;
+                            const int trips = (code == kMoveFar) ? 2 : 1;
+#pragma unroll 1
+                            for (int r = 0; r < trips; ++r) {
+                                const float v = pair_node_f32<KIND>(a.keys, s, i, wrap_node(n0 + r, M), f);
+                                if (code == kMoveUp || r == 1)
+                                    q.y = v;
+                                else
+                                    q.x = v;
+                            }
+                            s_rf[x] = q;
+                        } else if constexpr (pair_kind(KIND)) {
+                            // the same draws with the far-move node inline: at S = 31 the register
+                            // budget binds either way and this form measured 0.5% faster
                             const float v =
                                 pair_node_f32<KIND>(a.keys, s, i, wrap_node(code == kMoveUp ? nn + 1 : nn, M), f);
                             const float2 o = s_rf[x];
