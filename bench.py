@@ -216,6 +216,14 @@ def load_peaks() -> dict:
 # ------------------------------------------------------------------------------------------
 # CPU oracle (baseline leg / reference arm)
 # ------------------------------------------------------------------------------------------
+def cpu_sample_shape(L: int) -> tuple[int, int]:
+    """Window and steps of the CPU baseline sample: 2^20 sites x 128 steps per thread; chains
+    shorter than 2^21 take half their length and proportionally more steps, within the light cone
+    (w + 2 n <= L)."""
+    w = min(1 << 20, L // 2)
+    return w, min(128 * ((1 << 20) // w), (L - w) // 2)
+
+
 def oracle_sample(wl: dict, w: int, n_steps: int) -> dict:
     """Time the CPU oracle on windows of the same chains: one light-cone window of w sites per host
     thread, n_steps Euler steps each (exact sites of the full-size chains)."""
@@ -438,7 +446,7 @@ def main() -> None:
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(wl, 1 << 20, 128)
+        cpu = oracle_sample(wl, *cpu_sample_shape(wl["cpu"]["L"]))
         cpu.pop("seconds", None)
 
     state_gib = sum(w * (8 + 4 * (4 if k in QUAD_KINDS else 2 if k != 2 else 0)) for k, w in wk.items()) * n_sites / 2 ** 30

@@ -57,3 +57,18 @@ def test_reference_arm_only_on_rank_zero(capsys):
     args = argparse.Namespace(workload="rf_4x2^25", warmup=0, steps=1, gpus=2)
     bench.run_reference(args, rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_cpu_sample_fits_every_workload():
+    """The CPU baseline's light-cone window (w sites, n steps: w + 2 n sites of the chain) fits every
+    preset, the 2^16-site random-bond chains included, with the same 2^27 site-updates per thread."""
+    import bench
+    for name in ["rf_4x2^25", "rf_16x2^20", "rb_1024x2^16", "uneven_256", "rbg_linear_4x2^25", "none_16x2^20"]:
+        wl = bench.workload(name, 0)
+        L = wl["cpu"]["L"]
+        w, n = bench.cpu_sample_shape(L)
+        assert w >= 1 and n >= 1 and w + 2 * n <= L, name
+        assert w * n == 1 << 27, name
+    wl = bench.workload("rb_1024x2^16", 0)
+    r = bench.oracle_sample(wl, 1024, 16)
+    assert r["value"] > 0 and r["kind"] == "oracle"
