@@ -383,6 +383,18 @@ def main() -> None:
                         "peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured)"},
                 "fused_share_of_step": st["fused_ms"] / ms if ms > 0 else None}
 
+    # ---- measured lane-arithmetic rates (after the timed region): the peak above is derived from
+    # unit counts and the sampled clock; this shows what the device sustains on plain FMA chains ----
+    alu = q.measure_alu_peaks()
+    roofline["alu_measured"] = {
+        "fp32_fma_tops": alu["fp32_fma_per_s"] / 1e12, "sm_mhz": alu["sm_mhz"],
+        "frac_of_measured_fp32_fma": achieved / (alu["fp32_fma_per_s"] / 1e12),
+        "philox_blocks_per_s": alu["philox_blocks_per_s"],
+        "regeneration_bound_su_per_s": alu["philox_blocks_per_s"] / r_cross if r_cross > 0 else None,
+        "fp64_fma_tops": alu["fp64_fma_per_s"] / 1e12,
+        "basis": "qew_measure_alu_peaks: best of 3 event-timed launches of independent FMA chains / Philox4x32-10 "
+                 "blocks on a grid filling every SM"}
+
     # ---- structure factor (Eq. 6) of the relaxed chains: one call, outside the timed region ----
     sq = None
     if len(set(np.atleast_1d(wl["L"]).tolist())) == 1:

@@ -209,6 +209,22 @@ int qew_disorder_values(int32_t kind, int32_t precision, uint64_t seed, uint32_t
 int qew_philox_words(const uint32_t* ctr, const uint32_t* key, int64_t n_blocks, uint32_t* out);
 
 /*
+ * qew_measure_alu_peaks -- measured rates of the lane arithmetic on the current device, the
+ * denominators of the relaxation kernels' rooflines (the fused FP32-split kernel is bound by
+ * instruction issue, Sec. III.B's Euler scheme being a few operations per site and step):
+ *   out[0]  FP32 fused multiply-adds per second, summed over all lanes (independent chains on a
+ *           grid filling every SM): the lane-operation peak, nominally SMs x 128 x SM clock;
+ *   out[1]  FP64 fused multiply-adds per second (the plain FP64 comparison path);
+ *   out[2]  Philox4x32-10 blocks per second with a precomputed key schedule (the generator that
+ *           redraws the disorder at each cell crossing, Sec. III.B / IV.D);
+ *   out[3]  the SM clock in MHz during the FP32 run (cycle counter against the global timer).
+ * Each rate is the best of three event-timed launches after one untimed, on the legacy default
+ * stream; the call takes some tens of milliseconds and synchronises the device.  n_out >= 4
+ * (host array).  QEW_EINVAL for a NULL or short array; QEW_ECUDA if a CUDA call fails.
+ */
+int qew_measure_alu_peaks(double* out, int32_t n_out);
+
+/*
  * qew_enable_stats -- with enable != 0, bracket every launch of the fused FP32-split kernel with
  * CUDA events on the handle's stream and count cell crossings; 0 turns this off.  Counters
  * start from zero.

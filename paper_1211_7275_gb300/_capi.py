@@ -52,6 +52,7 @@ SIGNATURES = {
     "qew_disorder_values": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32,
                                            _P, _P, ctypes.c_int64, _P]),
     "qew_philox_words": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "qew_measure_alu_peaks": (ctypes.c_int, [_P, ctypes.c_int32]),
     "qew_enable_stats": (ctypes.c_int, [_H, ctypes.c_int32]),
     "qew_get_stats": (ctypes.c_int, [_H, _P, _P, _P, _P, _P]),
     "qew_observe_state_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,

@@ -171,3 +171,13 @@ def philox_words(ctr, key) -> np.ndarray:
     out = np.empty_like(ctr)
     _capi.check(lib.qew_philox_words(_ptr(ctr), _ptr(key), ctr.shape[0], _ptr(out)))
     return out
+
+
+def measure_alu_peaks() -> dict:
+    """Measured lane-arithmetic rates of the current device (qew_measure_alu_peaks): FP32 and FP64
+    FMAs per second over all lanes, Philox4x32-10 blocks per second, and the SM clock meanwhile."""
+    lib = _capi.load()
+    out = np.zeros(4)
+    _capi.check(lib.qew_measure_alu_peaks(_ptr(out), 4))
+    return {"fp32_fma_per_s": float(out[0]), "fp64_fma_per_s": float(out[1]), "philox_blocks_per_s": float(out[2]),
+            "sm_mhz": float(out[3])}
