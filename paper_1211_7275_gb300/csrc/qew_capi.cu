@@ -323,8 +323,8 @@ int build_layout(qew_ctx* h)
         d.f32 = static_cast<float>(h->f[c]);
         d.period = h->period;
         d.f64 = h->f[c];
-        for (int32_t st = 0; st < d.L; st += kBlockTile)
-            blocks.push_back(TileDesc{c, st});
+        for (int64_t st = 0; st < d.L; st += kBlockTile)   // 64-bit: L may reach 2^31 - 1
+            blocks.push_back(TileDesc{c, static_cast<int32_t>(st)});
         if (h->precision == QEW_FP32_SPLIT) {
             auto& lst = lists[d.kind];
             first[c] = static_cast<int32_t>(lst.size());

@@ -43,15 +43,15 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Chain-local index of window position x (window start wstart, |wstart| <= K).  A window wraps
 // at most once around a chain at least as long as the window; shorter chains take the modulo.
+// The wrap is taken in 64 bits: past the end of a chain of up to 2^31 - 1 sites, g itself may
+// not fit in an int32.
 __device__ __forceinline__ int32_t site_index(int64_t wstart, int x, bool contiguous, int32_t L)
 {
     const int64_t g = wstart + x;
     if (contiguous)
         return static_cast<int32_t>(g);
-    if (g >= -static_cast<int64_t>(L) && g < 2 * static_cast<int64_t>(L)) {
-        const int32_t r = static_cast<int32_t>(g);
-        return r < 0 ? r + L : (r >= L ? r - L : r);
-    }
+    if (g >= -static_cast<int64_t>(L) && g < 2 * static_cast<int64_t>(L))
+        return static_cast<int32_t>(g < 0 ? g + L : (g >= L ? g - L : g));
     return wrap_site(g, L);
 }
 

@@ -273,6 +273,29 @@ def test_full_size_sampled_sites(qew, orc):
     assert np.all(np.abs(dub - 0.1 * obs["v"][1]) <= 2e-6 * np.maximum(1, np.abs(obs["ubar"][1])))
 
 
+def test_maximum_chain_length(qew, orc):
+    """The longest chain the ABI accepts, L = 2^31 - 1 (int32 site index; 34 GB of FP32-split
+    state in two buffers): odd, so every tile width leaves a ragged tail, and its last windows wrap
+    around the seam at 2^31 - 1.  Sampled sites against the oracle's light-cone evaluation after
+    70 steps (two full K = 32 launches and a ragged one in the largest shape), and the invariant
+    dubar = dt v."""
+    L, n, f = (1 << 31) - 1, 70, 1.2
+    steps = np.array([0, n - 1, n])
+    with qew.Relaxation(L, f, RF, dt=0.1, seed=SEED, precision=FP32) as r:
+        r.set_tuning(1248, 32, 1)
+        obs = r.observe(steps)
+        u, _ = r.state()
+    w_own = 1248 - 64
+    rng = np.random.default_rng(5)
+    picks = [0, 1, 2, w_own - 1, w_own, L // 2, L - w_own, L - 3, L - 2, L - 1] + list(rng.integers(0, L, 4))
+    for i in picks:
+        ref_u, _ = orc.lightcone(L, 0, f, 0.1, RF, SEED, int(i), 1, n)
+        assert abs(u[i] - ref_u[0]) <= 1e-4, i
+    del u
+    dub = obs["ubar"][2] - obs["ubar"][1]
+    assert np.all(np.abs(dub - 0.1 * obs["v"][1]) <= 2e-6 * np.maximum(1, np.abs(obs["ubar"][1])))
+
+
 def test_full_size_autotuned_shape_is_bitwise_identical(qew):
     """The bench's launch configuration: on its 4 x 2^25 chains the autotuner picks a shape at
     step 1024.  The state after 1100 steps in that shape is bit for bit the state in the default
