@@ -269,15 +269,14 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
             const int qn = __shfl_sync(kFull, incl, 31);
             n_cross += (lane == 0) ? static_cast<unsigned>(qn) : 0u;
             if constexpr (KIND != kNone) {
-                const int excl = incl - cnt;
+                // each lane's walk resumes in the next chunk where it stopped
+                int q = incl - cnt;
+                MoveMask<S> m = mv;
                 for (int base = 0; base < qn; base += 32) {
-                    int q = excl;
-                    MoveMask<S> m = mv;
                     while (m != 0 && q < base + 32) {
                         const int b = mask_ffs(m) - 1;
                         m &= m - 1;
-                        if (q >= base)
-                            s_q[q - base] = (lane << 8) | b;
+                        s_q[q - base] = (lane << 8) | b;
                         ++q;
                     }
                     __syncwarp();

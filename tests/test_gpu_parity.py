@@ -296,6 +296,18 @@ def test_maximum_chain_length(qew, orc):
     assert np.all(np.abs(dub - 0.1 * obs["v"][1]) <= 2e-6 * np.maximum(1, np.abs(obs["ubar"][1])))
 
 
+def test_maximum_chain_length_fp64(qew, orc):
+    """The FP64 path on the same 2^31 - 1-site chain (one thread per site, neighbours wrapped at
+    the seam): sampled sites to 1e-12 after 20 steps."""
+    L, n, f = (1 << 31) - 1, 20, 1.2
+    with qew.Relaxation(L, f, RF, dt=0.1, seed=SEED, precision=FP64) as r:
+        r.observe([n])
+        u, _ = r.state()
+    for i in [0, 1, 1023, 1024, L // 2, L - 1025, L - 2, L - 1]:
+        ref_u, _ = orc.lightcone(L, 0, f, 0.1, RF, SEED, i, 1, n)
+        assert abs(u[i] - ref_u[0]) <= 1e-12 * max(1.0, abs(ref_u[0])), i
+
+
 def test_full_size_autotuned_shape_is_bitwise_identical(qew):
     """The bench's launch configuration: on its 4 x 2^25 chains the autotuner picks a shape at
     step 1024.  The state after 1100 steps in that shape is bit for bit the state in the default
