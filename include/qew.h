@@ -32,7 +32,8 @@
  *  - Pointers named *_out / *_in / steps / L / f / kind are HOST pointers owned by the caller;
  *    the library copies what it needs before returning.  Device memory is owned by the handle
  *    and freed by qew_destroy.
- *  - Calls on one handle must not run concurrently from several host threads.
+ *  - Calls on one handle must not run concurrently from several host threads; different
+ *    handles may be used from different threads at the same time.
  *  - Work is issued on the handle's stream (default: the legacy default stream, or the one set
  *    by qew_set_stream); calls that return host data synchronise that stream.
  *  - Time: after k Euler steps the chains are at t = k dt.  "step" always counts Euler steps

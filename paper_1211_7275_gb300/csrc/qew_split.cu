@@ -23,14 +23,16 @@
 // shuffles per neighbour and there is no block-wide barrier.
 //
 // Cell crossings: renormalisation is branch-free (n += floor(d), d -= floor(d)) and leaves one
-// bit per moved site.  After the update loop each lane stores its cells to shared memory (16-byte
-// stores; a store inside the update loop would keep the compiler from hoisting the cache loads
-// there), and a warp prefix sum of the lanes' move counts gives each
-// lane its queue slots, which it fills by walking the set bits of its mask (no atomics,
-// deterministic order).  The queued Philox values are then evaluated 32 lanes at a time and
+// bit per moved site.  After the update loop each lane stores its cells to shared memory (one
+// store per site; a store inside the update loop would keep the compiler from hoisting the cache
+// loads there), and a warp prefix sum of the lanes' move counts gives each lane its queue slots,
+// which it fills by walking the set bits of its mask, 32 slots per chunk, resuming in the next
+// chunk where it stopped (no atomics, deterministic order).  The queued Philox values are then
+// evaluated 32 lanes at a time and
 // written straight into the shared-memory cache of the requesting sites; the direction of each
 // move is recovered from the cell the cache was drawn for, kept per site in shared memory.
 #include <cstdio>
+#include <mutex>
 #include <type_traits>
 
 #include "qew_internal.h"
@@ -439,15 +441,24 @@ cudaError_t launch_split(int tiles_per_cta, const SplitLaunch& a, cudaStream_t s
 {
     const size_t smem = static_cast<size_t>(tiles_per_cta) * (32 * S * (8 + CacheBytes<KIND>::smem) + kQueueBytes);
     auto kern = split_step_kernel<KIND, S>;
-    // raise the dynamic shared-memory limit once per kernel and device to the largest shape in use
+    // raise the dynamic shared-memory limit of this kernel on this device to the largest shape in
+    // use; under a lock, so that two threads raising it at once cannot leave the smaller value
+    static std::mutex s_mu;
     static int s_limit[64] = {};
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && static_cast<int>(smem) > s_limit[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess)
-            return e;
-        s_limit[dev] = static_cast<int>(smem);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    {
+        std::lock_guard<std::mutex> g(s_mu);
+        const bool tracked = dev >= 0 && dev < 64;
+        if (!tracked || static_cast<int>(smem) > s_limit[dev]) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+            if (e != cudaSuccess)
+                return e;
+            if (tracked)
+                s_limit[dev] = static_cast<int>(smem);
+        }
     }
     const int grid = (a.n_tiles + tiles_per_cta - 1) / tiles_per_cta;
     if (grid == 0)

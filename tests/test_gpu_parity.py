@@ -329,6 +329,32 @@ def test_full_size_autotuned_shape_is_bitwise_identical(qew):
     np.testing.assert_array_equal(u_auto, u_default)
 
 
+def test_handles_on_concurrent_host_threads(qew):
+    """Different handles may run at the same time from different host threads (ctypes releases
+    the interpreter lock during each call): four threads with four tile shapes, whose first
+    launches raise the kernels' shared-memory limits concurrently, give the states of sequential
+    runs bit for bit."""
+    import threading
+    L, steps = 30000, np.array([0, 17, 400])
+    shapes = [(1248, 32, 1), (224, 8, 8), (992, 32, 2), (736, 16, 4)]
+    out, errs = [None] * len(shapes), []
+
+    def work(k):
+        try:
+            out[k] = gpu_run(qew, L, 1.1, RF, steps, FP32, tuning=shapes[k], seed=SEED + k)[1]
+        except Exception as e:  # pragma: no cover
+            errs.append(e)
+
+    ths = [threading.Thread(target=work, args=(k,)) for k in range(len(shapes))]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    assert not errs, errs
+    for k, sh in enumerate(shapes):
+        np.testing.assert_array_equal(out[k], gpu_run(qew, L, 1.1, RF, steps, FP32, tuning=sh, seed=SEED + k)[1])
+
+
 # ------------------------------------------------------------------------------------------
 # argument errors (need a device for handle creation)
 # ------------------------------------------------------------------------------------------
