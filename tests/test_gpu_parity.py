@@ -308,6 +308,46 @@ def test_maximum_chain_length_fp64(qew, orc):
         assert abs(u[i] - ref_u[0]) <= 1e-12 * max(1.0, abs(ref_u[0])), i
 
 
+def test_rf_at_the_paper_size_has_the_printed_shape(qew):
+    """The bench's 4 x 2^25 random-field chains at their f_c^L, 10^4 steps (t <= 10^3).
+    - The corrected-form fit of V (procedure (a) of Sec. IV.E) gives beta/nu z near the printed
+      0.128.
+    - The effective slopes over the last decade match the long-time values of Sec. IV.B:
+      -0.13 for v and 0.84 for w.
+    - The slope of w over the decade before is near the short-time 0.67.
+    - The amplitude is compared only in order of magnitude with the printed
+      v = 0.53 t^-0.128 [1 + (t/0.382)^-0.927] (Sec. IV.D). The paper does not give its
+      disorder strength, and the unit Gaussian here has a lower threshold (0.72 against 0.97).
+    - The corrected fit of w is not asserted: within t <= 10^3 its exponent is poorly determined.
+      The slope of w still rises through the window, and the fit extrapolates it (0.96 here, 1.02
+      for the oracle at L = 8192).
+    The oracle at L = 8192 (32 chains) gives -0.133 and 0.808 over the last decade."""
+    from paper_1211_7275_gb300 import std
+    from qew_workloads import preset_f
+    steps = log_spaced_steps(10_000, 60)
+    with qew.Relaxation(1 << 25, preset_f("rf_4x2^25"), RF, dt=0.1, seed=SEED, batch=4) as r:
+        r.set_tuning(0, 0, 0)
+        obs = r.observe(steps)
+    t = steps * 0.1
+    V, W = obs["v"].mean(1), np.sqrt(obs["w2"].mean(1))
+    fv = std.fit_corrected(t, V, t_mic=2.0)
+
+    def slope(y, a, b):
+        sel = (t >= a) & (t <= b)
+        return np.polyfit(np.log(t[sel]), np.log(y[sel]), 1)[0]
+
+    sv, sw, sw_short = slope(V, 100, 1000), slope(W, 100, 1000), slope(W, 10, 100)
+    sel = t >= 1.5
+    ratio = V[sel] / std.corrected(t[sel], 0.53, -0.128, 0.382, 0.927)
+    print(f"RF at 4 x 2^25: beta/nu z = {-fv['e']:.4f}; slopes over [100, 1000]: v {sv:.4f}, w {sw:.4f}; "
+          f"w over [10, 100] {sw_short:.4f}; V / printed fit in [{ratio.min():.3f}, {ratio.max():.3f}]")
+    assert 0.10 <= -fv["e"] <= 0.16
+    assert -0.15 <= sv <= -0.115
+    assert 0.74 <= sw <= 0.88
+    assert 0.60 <= sw_short <= 0.75
+    assert 0.3 <= ratio.min() and ratio.max() <= 3.0
+
+
 def test_full_size_autotuned_shape_is_bitwise_identical(qew):
     """The bench's launch configuration: on its 4 x 2^25 chains the autotuner picks a shape at
     step 1024.  The state after 1100 steps in that shape is bit for bit the state in the default
