@@ -71,6 +71,13 @@ __device__ __forceinline__ void tma_store_wait_all()
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
+// Wait until all committed bulk stores of this thread have finished reading their shared-memory
+// sources (the global writes may still be in flight).
+__device__ __forceinline__ void tma_store_wait_read_all()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
 // Bounded wait for phase `phase` of `bar`; false if `limit` polls did not see it complete.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int limit = kMbarSpinLimit)
 {
