@@ -63,17 +63,18 @@ struct CacheBytes {
     static constexpr int hbm = pair_kind(KIND) ? 8 : quad_kind(KIND) ? 16 : 0;
 };
 
-// Shared memory per site.  The random field uses a compact layout of 14 B: one 4-byte staging
-// slot (cells, then offsets, at load and store; each step's new cells in between), the 8-byte
-// node pair, and the low 16 bits of the cell the pair was drawn for.  At 992-site tiles this
-// fits 16 instead of 14 warps per SM (measured: +3.3%).  The other kinds keep 8 bytes of staging
-// (cell and offset side by side, the cell half doubling as the cache cell) plus their cache: the
-// node pair of Case 3 (8 B), whose small tiles are register-limited and lost 5% to the two-pass
-// staging; the four nodes and three coefficients of the cubic kinds (32 B).
-__host__ __device__ constexpr bool compact_kind(int kind) { return kind == kRF; }
-__host__ __device__ constexpr int site_smem_bytes(int kind)
+// Shared memory per site.  Random-field tiles of 31 or more sites per lane use a compact layout
+// of 14 B: one 4-byte staging slot (cells, then offsets, at load and store; each step's new
+// cells in between), the 8-byte node pair, and the low 16 bits of the cell the pair was drawn
+// for.  At 992-site tiles this fits 16 instead of 14 warps per SM (measured: +3.3%); smaller
+// tiles are register-limited, and there the two-pass staging only costs (measured on 736-site
+// random-field tiles in a mixed batch and on Case 3).  The other layouts keep 8 bytes of staging
+// (cell and offset side by side, the cell half doubling as the cache cell) plus the cache: a
+// node pair (8 B), or the four nodes and three coefficients of the cubic kinds (32 B).
+__host__ __device__ constexpr bool compact_layout(int kind, int S) { return kind == kRF && S >= 31; }
+__host__ __device__ constexpr int site_smem_bytes(int kind, int S)
 {
-    return compact_kind(kind) ? 4 + 8 + 2 : pair_kind(kind) ? 8 + 8 : quad_kind(kind) ? 8 + 32 : 8;
+    return compact_layout(kind, S) ? 4 + 8 + 2 : pair_kind(kind) ? 8 + 8 : quad_kind(kind) ? 8 + 32 : 8;
 }
 
 // Per warp after its sites: one chunk of 32 queued moves.
@@ -129,8 +130,8 @@ template <int KIND, int S>
 __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_kernel(SplitLaunch a)
 {
     constexpr int TW = 32 * S;
-    constexpr bool kCompact = compact_kind(KIND);
-    constexpr int WARP_SMEM = TW * site_smem_bytes(KIND) + kQueueBytes;
+    constexpr bool kCompact = compact_layout(KIND, S);
+    constexpr int WARP_SMEM = TW * site_smem_bytes(KIND, S) + kQueueBytes;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t s_bar[8];
 
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     // offsets' slot of each site takes its cell after the step (relative to N0, as a float).
     int32_t* s_ccell = s_cell;
     float* s_newc = s_off;
-    int* s_q = reinterpret_cast<int*>(wsm + TW * site_smem_bytes(KIND));   // request chunk
+    int* s_q = reinterpret_cast<int*>(wsm + TW * site_smem_bytes(KIND, S));   // request chunk
     // compact layout: staging at 0, the node pair at 4 TW, cache cells (low 16 bits) at 12 TW
     float2* s_rf = reinterpret_cast<float2*>(wsm + (kCompact ? 4 : 8) * TW);
     uint16_t* s_cc16 = reinterpret_cast<uint16_t*>(wsm + 12 * TW);
@@ -170,8 +171,8 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     // Contiguous, 16-byte aligned windows arrive by TMA bulk copies (one per array, completion
     // on the warp's mbarrier); windows that wrap around the chain or start unaligned use
     // coalesced read-only loads.
-    // The compact layout (random field) stages cells and offsets one after the other through the
-    // same slot: cells (with the node pairs) first, then offsets.
+    // The compact layout stages cells and offsets one after the other through the same slot:
+    // cells (with the node pairs) first, then offsets.
     const bool tma_in = contiguous && (((ch.offset + wstart) & 3) == 0);
     const int64_t p0 = ch.offset + wstart;
     uint64_t* bar = &s_bar[warp];
@@ -542,7 +543,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
 template <int KIND, int S>
 cudaError_t launch_split(int tiles_per_cta, const SplitLaunch& a, cudaStream_t st)
 {
-    const size_t smem = static_cast<size_t>(tiles_per_cta) * (32 * S * site_smem_bytes(KIND) + kQueueBytes);
+    const size_t smem = static_cast<size_t>(tiles_per_cta) * (32 * S * site_smem_bytes(KIND, S) + kQueueBytes);
     auto kern = split_step_kernel<KIND, S>;
     // raise the dynamic shared-memory limit of this kernel on this device to the largest shape in
     // use; under a lock, so that two threads raising it at once cannot leave the smaller value
@@ -643,7 +644,7 @@ bool split_supported(int kind, int S)
 
 size_t split_smem_bytes(int kind, int S, int tiles_per_cta)
 {
-    return static_cast<size_t>(tiles_per_cta) * (32 * S * site_smem_bytes(kind) + kQueueBytes);
+    return static_cast<size_t>(tiles_per_cta) * (32 * S * site_smem_bytes(kind, S) + kQueueBytes);
 }
 
 cudaError_t split_step(int kind, int S, int tiles_per_cta, const SplitLaunch& a, cudaStream_t st)
