@@ -76,7 +76,8 @@ enum qew_precision {
 /*
  * qew_create -- `batch` chains of `L` sites, samples s = 0 .. batch-1, all with drive `f` and
  * disorder `disorder_kind`, time step `dt`, flat start, precision QEW_FP32_SPLIT.
- * Requirements: 1 <= L < 2^31, batch >= 1, L * batch < 2^40, 0 < dt < 0.5, f finite.
+ * Requirements: 1 <= L < 2^31, batch >= 1, L * batch < 2^40, 0 < dt < 0.5, |f| < 2^12 (so that,
+ * with neighbouring displacements below 2^12, no Euler step moves a site by 2^15 cells or more).
  * Allocates the state on the current CUDA device (QEW_ENOMEM if it does not fit).
  * On success *out receives the handle; on failure *out is set to NULL.
  */

@@ -650,8 +650,8 @@ int create_impl(qew_handle* out, int32_t n_chains, const int64_t* L, const doubl
     for (int32_t c = 0; c < n_chains; ++c) {
         if (L[c] < 1 || L[c] >= (int64_t(1) << 31))
             return fail(nullptr, QEW_EINVAL, "chain length " + std::to_string(L[c]) + " outside [1, 2^31)");
-        if (!std::isfinite(f[c]))
-            return fail(nullptr, QEW_EINVAL, "drive f must be finite");
+        if (!std::isfinite(f[c]) || std::fabs(f[c]) >= 4096.0)
+            return fail(nullptr, QEW_EINVAL, "drive f must be finite with |f| < 2^12");
         if (kind[c] < QEW_RF_GAUSS_LINEAR || kind[c] > QEW_RB_GAUSS_CATMULLROM)
             return fail(nullptr, QEW_EINVAL, "unknown disorder kind " + std::to_string(kind[c]));
         total += L[c];

@@ -50,6 +50,8 @@ def test_argument_errors_without_device(lib):
     assert lib.qew_create(ctypes.byref(h), 16, 1, 1.0, 0.7, 0, 1) == -1
     assert b"dt" in lib.qew_last_error(None)
     assert lib.qew_create(ctypes.byref(h), 16, 1, float("nan"), 0.1, 0, 1) == -1
+    assert lib.qew_create(ctypes.byref(h), 16, 1, 4096.0, 0.1, 0, 1) == -1
+    assert b"|f| < 2^12" in lib.qew_last_error(None)
     assert lib.qew_create(ctypes.byref(h), 16, 1, 1.0, 0.1, 7, 1) == -1
     assert lib.qew_create(ctypes.byref(h), 1 << 31, 1, 1.0, 0.1, 0, 1) == -1
     assert lib.qew_create(None, 16, 1, 1.0, 0.1, 0, 1) == -1
