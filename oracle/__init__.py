@@ -18,7 +18,9 @@ Functions and the passages they follow:
                      through G (Case 3), Sec. III.B and Sec. IV.C.
   rb_potential       the RB spline potential itself (spline pins only).
   run                Euler integration of Eq. 1 (eta = c = 1, periodic in x, Sec. III.B) from
-                     the flat start (Sec. II) or a given state, with v, ubar, w2 of Eqs. 3-5.
+                     the flat start (Sec. II) or a given state, with v, ubar, w2 of Eqs. 3-5;
+                     ``node_f32=True`` runs the same FP64 dynamics with every disorder value
+                     rounded to FP32 (the floor of any FP32 store of the disorder).
   lightcone          the same dynamics evaluated on a window of 2n+w sites, exact for the
                      w central sites after n steps (stencil radius 1).
   structure_factor   S_q of Eq. 6 (Sec. II): the sample mean of |(1/L) sum_x u(x) e^{-iqx}|^2
@@ -79,7 +81,8 @@ def _load():
                                                 ctypes.c_int64, P, ctypes.c_int64]
             lib.oracle_rb_potential.restype = None
             lib.oracle_run.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.c_double, ctypes.c_uint64, P, P,
-                                       ctypes.c_int32, P, P, P, P, ctypes.c_int32, ctypes.c_int64]
+                                       ctypes.c_int32, P, P, P, P, ctypes.c_int32, ctypes.c_int64,
+                                       ctypes.c_int32]
             lib.oracle_run.restype = ctypes.c_int
             lib.oracle_lightcone.argtypes = [ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
@@ -133,14 +136,15 @@ def rb_potential(seed: int, s: int, i, u, kind: int = KIND_RB, period: int = 0) 
 
 
 def run(L, f, dt: float, kind, seed: int, steps, *, s=None, u0=None, n_threads: int = 0,
-        want_state: bool = False, period: int = 0) -> dict:
+        want_state: bool = False, period: int = 0, node_f32: bool = False) -> dict:
     """Relax independent periodic chains and observe them at ``steps``.
 
     ``L``, ``f``, ``kind`` and ``s`` are per-chain sequences (scalars broadcast); ``s``
     defaults to 0..n_chains-1.  ``u0`` is the concatenated initial state (default: flat).
     Returns ``v``, ``ubar``, ``w2`` as [n_times, n_chains] and, with ``want_state``, the
     concatenated final state ``u``.  ``period`` > 0 makes the disorder periodic in u with that
-    period (the L x M system of Sec. III.B).
+    period (the L x M system of Sec. III.B).  ``node_f32`` rounds every disorder value to FP32
+    before it enters the force (the FP32 node model; the dynamics stays FP64).
     """
     L = np.atleast_1d(np.asarray(L, dtype=np.int64))
     n_chains = L.shape[0]
@@ -164,7 +168,7 @@ def run(L, f, dt: float, kind, seed: int, steps, *, s=None, u0=None, n_threads: 
     rc = _load().oracle_run(n_chains, _p(L), _p(s), _p(f), _p(kind), dt, seed,
                             _p(u_in) if u_in is not None else None, _p(steps), nt,
                             _p(v), _p(ub), _p(w2), _p(u_out) if u_out is not None else None, n_threads,
-                            int(period))
+                            int(period), 1 if node_f32 else 0)
     if rc != 0:
         raise ValueError(f"oracle_run failed with status {rc}")
     out = {"v": v, "ubar": ub, "w2": w2}

@@ -42,6 +42,12 @@
  *   R, G = sqrt(-2 ln U_1) cos(2 pi U_2)   (Box and Muller 1958, cosine branch)
  *   V = (x_0 + 1/2) 2^-31 - 1.
  *
+ * FP32 node model (oracle_run with node_f32 = 1): the same dynamics, in FP64, with every
+ * disorder value rounded to the nearest FP32 number before it enters the force.  This is the
+ * exact dynamics of the disorder as any FP32 store of it holds it; comparing it with the exact
+ * run measures how far the rounding of the disorder alone moves the line (near the depinning
+ * threshold it is amplified), which is the floor of every FP32 implementation.
+ *
  * Build: gcc -O2 -std=c11 -fPIC -shared -ffp-contract=off (no fused multiply-add, so the
  * rounding sequence is the one written here on every host).
  */
@@ -156,8 +162,17 @@ static double potential_value(int kind, uint64_t seed, uint32_t s, int64_t i, in
     return kind == QO_RB ? rb_value(seed, s, i, n) : rbg_value(seed, s, i, n);
 }
 
-/* Pinning force at site i of chain s and displacement u (Sec. III.B, Sec. IV.C). */
-static double pinning_force(int kind, uint64_t seed, uint32_t s, int64_t i, double u, int64_t period)
+/* A disorder value as the force sees it: exact, or rounded to the nearest FP32 number (the
+   FP32 node model; the conversion rounds to nearest, ties to even). */
+static double node_value(double v, int node_f32)
+{
+    return node_f32 ? (double)(float)v : v;
+}
+
+/* Pinning force at site i of chain s and displacement u (Sec. III.B, Sec. IV.C); with
+   node_f32 every disorder value is rounded to FP32 first. */
+static double pinning_force_nodes(int kind, uint64_t seed, uint32_t s, int64_t i, double u, int64_t period,
+                                  int node_f32)
 {
     if (kind == QO_NONE)
         return 0.0;
@@ -165,26 +180,32 @@ static double pinning_force(int kind, uint64_t seed, uint32_t s, int64_t i, doub
     int64_t n = (int64_t)fl;
     double d = u - fl;
     if (kind == QO_RF) {
-        double r0 = rf_value(seed, s, i, wrap_node(n, period));
-        double r1 = rf_value(seed, s, i, wrap_node(n + 1, period));
+        double r0 = node_value(rf_value(seed, s, i, wrap_node(n, period)), node_f32);
+        double r1 = node_value(rf_value(seed, s, i, wrap_node(n + 1, period)), node_f32);
         return (1.0 - d) * r0 + d * r1;
     }
     if (kind == QO_RBG_LINEAR) {
         /* V(u) = (1 - d) G(n) + d G(n+1) on [n, n+1), so -dV/du = G(n) - G(n+1) */
-        return rbg_value(seed, s, i, wrap_node(n, period)) - rbg_value(seed, s, i, wrap_node(n + 1, period));
+        return node_value(rbg_value(seed, s, i, wrap_node(n, period)), node_f32) -
+               node_value(rbg_value(seed, s, i, wrap_node(n + 1, period)), node_f32);
     }
     /* RB / RB-G cubic: V(u) on [n, n+1] is the uniform Catmull-Rom cubic through
        p0..p3 = V(n-1..n+2):
        V(d) = 1/2 [2 p1 + (p2 - p0) d + (2p0 - 5p1 + 4p2 - p3) d^2 + (-p0 + 3p1 - 3p2 + p3) d^3]
        and F = -dV/du. */
-    double p0 = potential_value(kind, seed, s, i, n - 1, period);
-    double p1 = potential_value(kind, seed, s, i, n, period);
-    double p2 = potential_value(kind, seed, s, i, n + 1, period);
-    double p3 = potential_value(kind, seed, s, i, n + 2, period);
+    double p0 = node_value(potential_value(kind, seed, s, i, n - 1, period), node_f32);
+    double p1 = node_value(potential_value(kind, seed, s, i, n, period), node_f32);
+    double p2 = node_value(potential_value(kind, seed, s, i, n + 1, period), node_f32);
+    double p3 = node_value(potential_value(kind, seed, s, i, n + 2, period), node_f32);
     double a = p2 - p0;
     double b = ((2.0 * p0 - 5.0 * p1) + 4.0 * p2) - p3;
     double c = ((3.0 * p1 - p0) - 3.0 * p2) + p3;
     return -0.5 * ((a + 2.0 * b * d) + 3.0 * c * d * d);
+}
+
+static double pinning_force(int kind, uint64_t seed, uint32_t s, int64_t i, double u, int64_t period)
+{
+    return pinning_force_nodes(kind, seed, s, i, u, period, 0);
 }
 
 /* The RB potential itself, V(i, u), for the spline pins: Catmull-Rom (RB, RB-G cubic) or
@@ -280,6 +301,7 @@ typedef struct {
     int kind;
     uint64_t seed;
     int64_t period;        /* disorder period M in u (0: aperiodic) */
+    int node_f32;          /* 1: disorder values rounded to FP32 (the FP32 node model) */
     const double* u0;      /* initial state [L] or NULL for the flat start */
     const int64_t* steps;  /* observation steps, strictly increasing, >= 0 */
     int32_t n_times;
@@ -308,7 +330,7 @@ static int run_chain(chain_job_t* job)
         int64_t target = job->steps[k];
         for (;;) {
             for (int64_t i = 0; i < L; ++i)
-                F[i] = pinning_force(job->kind, job->seed, job->s, i, u[i], job->period);
+                F[i] = pinning_force_nodes(job->kind, job->seed, job->s, i, u[i], job->period, job->node_f32);
             if (step == target)
                 break;
             for (int64_t i = 0; i < L; ++i) {
@@ -390,13 +412,14 @@ static int run_jobs(chain_job_t* jobs, int32_t n_jobs, int32_t n_threads)
  * and disorder kind kind[c]; the disorder is periodic in u with period `period` (0:
  * aperiodic).  Observations at steps[0..n_times) are written to
  * v_out/ubar_out/w2_out[k * n_chains + c].  u0 (optional) and u_final (optional) hold the
- * chains one after another (chain c starts at offset sum_{c'<c} L[c']).
+ * chains one after another (chain c starts at offset sum_{c'<c} L[c']).  node_f32 = 1 runs
+ * the FP32 node model (disorder values rounded to FP32); 0 the exact dynamics.
  * Returns 0, or -1 on bad arguments, -2 on allocation failure.
  */
 int oracle_run(int32_t n_chains, const int64_t* L, const uint32_t* s, const double* f, const int32_t* kind,
                double dt, uint64_t seed, const double* u0, const int64_t* steps, int32_t n_times,
                double* v_out, double* ubar_out, double* w2_out, double* u_final, int32_t n_threads,
-               int64_t period)
+               int64_t period, int32_t node_f32)
 {
     if (n_chains < 1 || n_times < 0)
         return -1;
@@ -419,6 +442,7 @@ int oracle_run(int32_t n_chains, const int64_t* L, const uint32_t* s, const doub
         jobs[c].kind = kind[c];
         jobs[c].seed = seed;
         jobs[c].period = period;
+        jobs[c].node_f32 = node_f32 != 0;
         jobs[c].u0 = u0 ? u0 + off : NULL;
         jobs[c].steps = steps;
         jobs[c].n_times = n_times;

@@ -16,6 +16,9 @@ Spline pins: the RF force interpolates R linearly between integers (Sec. III.B, 
     the linear spline through G, constant inside a cell, and equals the cell average of the
     Case 1 force through the same G (both potentials take the same values at the integers).
 Observables: ubar, w2 against numpy's mean and population variance (Eqs. 4-5).
+FP32 node model: the oracle's dynamics with every disorder value rounded to the nearest FP32
+    number (the floor of any FP32 store of the disorder): one step from flat written out with
+    numpy's float32 rounding, and 40 steps against a plain numpy restatement.
 """
 import math
 
@@ -239,3 +242,52 @@ def test_rejects_bad_arguments(orc):
         orc.run(0, 1.0, 0.1, 0, SEED, [1])
     with pytest.raises(ValueError):
         orc.lightcone(10, 0, 1.0, 0.1, 0, SEED, 0, 3, 4)
+
+
+# ------------------------------------------------------------------------------------------
+# FP32 node model: the exact dynamics of the disorder rounded to FP32
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", [0, 1, 3, 4])
+def test_fp32_node_model_first_step(orc, kind):
+    """From the flat start (lap = 0, d = 0) one step of the FP32 node model is
+    u_i(1) = dt ((0 + f) + F), with F formed from the disorder values rounded to the nearest
+    FP32 number (numpy's float32 conversion, round to nearest even): R(0) for RF, G(0) - G(1)
+    for Case 3, -(V(1) - V(-1)) / 2 for the Catmull-Rom kinds."""
+    L, f, dt, s = 211, 0.8, 0.1, 2
+    i = np.arange(L)
+
+    def node(n):
+        return orc.disorder_values(kind, SEED, s, i, np.full(L, n)).astype(np.float32).astype(np.float64)
+
+    if kind == 0:
+        F = node(0)
+    elif kind == 3:
+        F = node(0) - node(1)
+    else:
+        F = -0.5 * (node(1) - node(-1))
+    out = orc.run(L, f, dt, kind, SEED, [1], s=[s], want_state=True, node_f32=True)
+    assert np.array_equal(out["u"], dt * ((0.0 + f) + F))
+    exact = orc.run(L, f, dt, kind, SEED, [1], s=[s], want_state=True)
+    assert not np.array_equal(out["u"], exact["u"])          # the rounding is applied ...
+    assert np.max(np.abs(out["u"] - exact["u"])) <= dt * 2.0 ** -23 * 8   # ... and is an FP32 rounding
+
+
+def test_fp32_node_model_moves_cells(orc):
+    """Later steps of the FP32 node model use the rounded values of the cell each site has moved
+    to: after 40 steps the exact run's state and the node model agree to the size the rounding
+    can explain, and the node model equals a plain numpy restatement with rounded nodes."""
+    L, f, dt, s, n = 64, 1.3, 0.1, 5, 40
+    out = orc.run(L, f, dt, 0, SEED, [n], s=[s], want_state=True, node_f32=True)["u"]
+    u = np.zeros(L)
+    i = np.arange(L)
+    for _ in range(n):
+        c = np.floor(u)
+        d = u - c
+        r0 = orc.disorder_values(0, SEED, s, i, c).astype(np.float32).astype(np.float64)
+        r1 = orc.disorder_values(0, SEED, s, i, c + 1).astype(np.float32).astype(np.float64)
+        F = (1.0 - d) * r0 + d * r1
+        lap = (np.roll(u, -1) + np.roll(u, 1)) - 2.0 * u
+        u = u + dt * ((lap + f) + F)
+    assert np.array_equal(out, u)
+    exact = orc.run(L, f, dt, 0, SEED, [n], s=[s], want_state=True)["u"]
+    assert 0 < np.max(np.abs(out - exact)) < 1e-5
