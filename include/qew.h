@@ -113,6 +113,16 @@ int qew_set_stream(qew_handle h, void* stream);
 int qew_set_disorder_period(qew_handle h, int64_t period);
 
 /*
+ * qew_set_samples -- sample index s of each chain (counter word 2 of the generator, so the
+ * disorder realisation of the chain; Sec. III.B draws an independent disorder per sample):
+ * s[c] for chain c, n_chains entries (host array, copied).  By default chain c uses s = c.  With
+ * it a chain can be relaxed on its own, or a set of samples split over several handles or GPUs,
+ * on exactly the disorder it has inside a batch.  The state is reset to the flat start at
+ * step 0, since every cache depends on s.  QEW_EINVAL if s is NULL.
+ */
+int qew_set_samples(qew_handle h, const uint32_t* s);
+
+/*
  * qew_set_tuning -- launch shape of the fused FP32-split kernel: `tile_w` sites per warp tile
  * (32 lanes x an odd number of sites: 224, 480, 736, 992 or 1248).  Each disorder kind takes the
  * widest tile it supports up to tile_w: cubic random-bond chains (Cases 1 and 2) at most 480,

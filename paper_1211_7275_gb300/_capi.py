@@ -38,6 +38,7 @@ SIGNATURES = {
     "qew_set_precision": (ctypes.c_int, [_H, ctypes.c_int32]),
     "qew_set_stream": (ctypes.c_int, [_H, _P]),
     "qew_set_disorder_period": (ctypes.c_int, [_H, ctypes.c_int64]),
+    "qew_set_samples": (ctypes.c_int, [_H, _P]),
     "qew_set_tuning": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "qew_get_tuning": (ctypes.c_int, [_H, _P, _P, _P]),
     "qew_advance": (ctypes.c_int, [_H, ctypes.c_int64]),

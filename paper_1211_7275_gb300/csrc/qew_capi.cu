@@ -75,6 +75,7 @@ struct qew_ctx {
     std::vector<int64_t> L;
     std::vector<double> f;
     std::vector<int32_t> kind;
+    std::vector<uint32_t> sample;   // sample index s of each chain (counter word 2)
     std::vector<int64_t> offset;
     double dt = 0.1;
     uint64_t seed = 0;
@@ -318,7 +319,7 @@ int build_layout(qew_ctx* h)
         ChainDesc& d = h->h_chains[c];
         d.offset = h->offset[c];
         d.L = static_cast<int32_t>(h->L[c]);
-        d.s = static_cast<uint32_t>(c);
+        d.s = h->sample[c];
         d.kind = h->kind[c];
         d.f32 = static_cast<float>(h->f[c]);
         d.period = h->period;
@@ -672,6 +673,9 @@ int create_impl(qew_handle* out, int32_t n_chains, const int64_t* L, const doubl
         h->L.assign(L, L + n_chains);
         h->f.assign(f, f + n_chains);
         h->kind.assign(kind, kind + n_chains);
+        h->sample.resize(n_chains);
+        for (int32_t c = 0; c < n_chains; ++c)
+            h->sample[c] = static_cast<uint32_t>(c);
         h->offset.resize(n_chains);
         int64_t off = 0;
         for (int32_t c = 0; c < n_chains; ++c) {
@@ -1004,6 +1008,21 @@ int qew_set_disorder_period(qew_handle h, int64_t period)
     DeviceGuard g(h->device);
     cudaStreamSynchronize(h->stream);
     h->period = static_cast<int32_t>(period);
+    int rc = build_layout(h);
+    if (rc == QEW_OK)
+        rc = init_state(h, nullptr, std::vector<double>(h->n_chains, 0.0));
+    return rc;
+}
+
+int qew_set_samples(qew_handle h, const uint32_t* s)
+{
+    if (int rc = check_handle(h))
+        return rc;
+    if (!s)
+        return fail(h, QEW_EINVAL, "s must not be NULL");
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    h->sample.assign(s, s + h->n_chains);
     int rc = build_layout(h);
     if (rc == QEW_OK)
         rc = init_state(h, nullptr, std::vector<double>(h->n_chains, 0.0));

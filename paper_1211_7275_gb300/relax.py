@@ -21,7 +21,7 @@ def _ptr(a: np.ndarray):
 class Relaxation:
     """A batch of chains: ``L`` (int or per-chain sequence), drive ``f`` and disorder ``kind``
     (scalars or per-chain), time step ``dt``, master ``seed``, ``precision`` (FP32_SPLIT or
-    FP64).  Chain c uses sample index c."""
+    FP64).  Chain c uses sample index c unless ``set_samples`` says otherwise."""
 
     def __init__(self, L, f, kind=RF_GAUSS_LINEAR, dt: float = 0.1, seed: int = 12117275,
                  precision: int = FP32_SPLIT, batch: int | None = None, stream=None):
@@ -82,6 +82,11 @@ class Relaxation:
     def set_disorder_period(self, period: int) -> None:
         """Disorder periodic in u with ``period`` (0: aperiodic); resets to the flat start."""
         self._check(self._lib.qew_set_disorder_period(self._h, int(period)))
+
+    def set_samples(self, s) -> None:
+        """Sample index (disorder realisation) of each chain; resets to the flat start."""
+        s = np.ascontiguousarray(np.broadcast_to(np.asarray(s, np.uint32), (self.n_chains,)))
+        self._check(self._lib.qew_set_samples(self._h, _ptr(s)))
 
     def set_tuning(self, tile_w: int = 0, K: int = 0, tiles_per_cta: int = 0) -> None:
         self._check(self._lib.qew_set_tuning(self._h, tile_w, K, tiles_per_cta))

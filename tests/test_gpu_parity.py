@@ -155,26 +155,42 @@ def test_split_uneven_mixed_batch(qew, orc):
 
 
 def test_split_near_critical_precision(qew, orc):
-    """At f = f_c^L (random field, L = 4096, the oracle-bisected fixture) the FP32 rounding of the
-    disorder values and of the force is amplified at the rare sites that sit near a depinning
-    threshold; the deviation from the FP64 oracle over the first 10^3 steps is checked as a
-    distribution: rms, the fraction of sites above 1e-4, and the maximum.  Bounds: the FP32
-    precision measured for this kernel (rms 1.6e-5, 0.23% of sites above 1e-4, max 7.7e-4 on the
-    first GB300 run) with headroom; an emulation with correctly rounded FP32 disorder values and
-    otherwise exact arithmetic already reaches ~5e-5 at the worst site of 4 chains."""
+    """Random field at f = f_c^L (L = 4096, the oracle-bisected fixture), 16 chains, per site
+    against the FP64 oracle.  Near the depinning threshold the dynamics amplifies any change of
+    the force: the FP32 node model (the oracle's exact dynamics with each disorder value rounded
+    to FP32, the floor of any FP32 store of the disorder) itself moves 28 of these 65536 sites by
+    more than 1e-4 by step 1000 (max 5.0e-4), while through step 200 it stays below 2e-5.  So the
+    per-site bar of 1e-4 is asked where the arithmetic can meet it:
+      - through step 200, at every site;
+      - at step 1000, at every site that the FP32 node model leaves within 1e-5 of the exact run
+        (sites insensitive to the rounding at this horizon, 99.2% of them);
+    and over all sites at step 1000 the distribution is bounded: rms <= 2e-5, at most 0.1% of
+    sites above 1e-4, max <= 1e-3."""
     import json
     import os
     with open(os.path.join(os.path.dirname(__file__), "golden", "fc_rf_L4096.json")) as fh:
         fc = json.load(fh)
-    L, f, n = fc["L"], fc["f_c"], 1000
-    with qew.Relaxation(L, f, RF, dt=0.1, seed=SEED, precision=FP32, batch=4) as r:
-        r.observe([n])
-        u, _ = r.state()
-    ref = orc.run([L] * 4, f, 0.1, RF, SEED, [n], want_state=True)["u"]
-    err = np.abs(u - ref)
-    rms, frac, mx = float(np.sqrt(np.mean(err ** 2))), float(np.mean(err > 1e-4)), float(err.max())
-    print(f"near-critical FP32-split vs oracle after {n} steps: rms {rms:.2e}, >1e-4: {frac:.1e}, max {mx:.2e}")
-    assert rms <= 3e-5 and frac <= 1e-2 and mx <= 3e-3, (rms, frac, mx)
+    L, f, B = fc["L"], fc["f_c"], 16
+    with qew.Relaxation(L, f, RF, dt=0.1, seed=SEED, precision=FP32, batch=B) as r:
+        r.observe([200])
+        u200, _ = r.state()
+        r.observe([1000])
+        u1000, _ = r.state()
+    for n, u in ((200, u200), (1000, u1000)):
+        ref = orc.run([L] * B, f, 0.1, RF, SEED, [n], want_state=True)["u"]
+        floor = orc.run([L] * B, f, 0.1, RF, SEED, [n], want_state=True, node_f32=True)["u"]
+        err, ef = np.abs(u - ref), np.abs(floor - ref)
+        rms, frac, mx = float(np.sqrt(np.mean(err ** 2))), float(np.mean(err > 1e-4)), float(err.max())
+        calm = ef <= 1e-5
+        print(f"step {n}: FP32-split vs oracle rms {rms:.2e}, >1e-4: {frac:.1e}, max {mx:.2e}; FP32 node model "
+              f"rms {np.sqrt(np.mean(ef ** 2)):.2e}, >1e-4: {np.mean(ef > 1e-4):.1e}, max {ef.max():.2e}; "
+              f"max on the {calm.mean():.4f} insensitive sites {err[calm].max():.2e}")
+        if n == 200:
+            assert mx <= 1e-4, mx
+        else:
+            assert calm.mean() >= 0.98
+            assert err[calm].max() <= 1e-4, err[calm].max()
+            assert rms <= 2e-5 and frac <= 1e-3 and mx <= 1e-3, (rms, frac, mx)
 
 
 def test_split_closed_form(qew):
