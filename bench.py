@@ -60,6 +60,10 @@ def parse():
     p.add_argument("--n-obs", type=int, default=12)
     p.add_argument("--tuning", default="auto", help="'auto' or tile_w,K,tiles_per_cta")
     p.add_argument("--fp64-steps", type=int, default=256, help="Euler steps of the FP64 comparison leg (0: skip)")
+    p.add_argument("--horizon-steps", type=int, default=None,
+                   help="Euler steps of the one relaxation timed at the workload's own horizon, outside the timed "
+                        "loop (default: the preset's n_steps, 2^20 for rf_4x2^25; 0: skip)")
+    p.add_argument("--horizon-obs", type=int, default=None, help="observations of that relaxation (default: the preset's)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -395,15 +399,69 @@ def main() -> None:
         "basis": "qew_measure_alu_peaks: best of 3 event-timed launches of independent FMA chains / Philox4x32-10 "
                  "blocks on a grid filling every SM"}
 
-    # ---- structure factor (Eq. 6) of the relaxed chains: one call, outside the timed region ----
+    # ---- one relaxation at the workload's own horizon (its preset's steps and observation count),
+    # outside the timed loop: the crossing rate, and with it the speed, changes with t ----
+    horizon = None
+    h_steps = W.PRESETS[wl["name"]].get("n_steps", 0) if args.horizon_steps is None else args.horizon_steps
+    if h_steps > 0:
+        h_obs = args.horizon_obs or W.PRESETS[wl["name"]].get("n_obs", 100)
+        hs = W.log_spaced_steps(h_steps, h_obs)
+        split = min(h_steps, 1 << 16)   # the late part (steps past 2^16) is reported on its own
+        parts = [hs[hs <= split], hs[hs > split]]
+        relax.reset()
+        relax.enable_stats(True)
+        hsamp = ClockSampler(bus_id(local))
+        torch.cuda.synchronize()
+        hsamp.start()
+        legs = []
+        for part in parts:
+            if part.size == 0:
+                continue
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            relax.observe(part)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            hst = relax.stats()
+            legs.append((e0.elapsed_time(e1), hst))
+        hclk = hsamp.stop()
+        relax.enable_stats(False)
+        hpeak = sms * LANES_PER_SM * ((hclk or {}).get("sm_mhz") or clk) * 1e6 / 1e12
+
+        def leg_fields(ms_leg, hst, steps):
+            rx = hst["crossings"] / max(1, hst["site_updates"])
+            ops = sum(w * (OPS_BASE[k] + OPS_PER_CROSSING[k] * rx) for k, w in wk.items())
+            ach = ops * hst["site_updates"] / (hst["fused_ms"] / 1e3) / 1e12 if hst["fused_ms"] > 0 else None
+            return {"steps": int(steps), "ms": ms_leg, "value": n_sites * steps / (ms_leg / 1e3),
+                    "crossings_per_site_update": rx, "ops_per_site_update": ops,
+                    "roofline_frac": (ach / hpeak) if ach else None,
+                    "fused_share": hst["fused_ms"] / ms_leg if ms_leg > 0 else None}
+
+        ms_h = sum(m for m, _ in legs)
+        tot = {k: sum(h[k] for _, h in legs) for k in ("crossings", "site_updates", "fused_ms")}
+        horizon = {"relax_steps": int(h_steps), "observations": int(hs.size), **leg_fields(ms_h, tot, h_steps),
+                   "unit": UNIT, "peak": hpeak, "clocks": hclk,
+                   "note": "one relaxation from the flat start, fused observations at the preset's log-spaced "
+                           "steps, launch shape of the timed loop; value = site-updates / device time"}
+        if len(legs) == 2:
+            horizon["early"] = leg_fields(legs[0][0], legs[0][1], split)
+            horizon["late"] = leg_fields(legs[1][0], legs[1][1], h_steps - split)
+
+    # ---- structure factor (Eq. 6) of the relaxed chains, outside the timed region: the first call
+    # builds the cuFFT plan; the second shows the steady state ----
     sq = None
     if len(set(np.atleast_1d(wl["L"]).tolist())) == 1:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        S = relax.structure_factor()
-        sq = {"ms": 1e3 * (time.perf_counter() - t0), "modes": int(S.size), "chains": int(wl["n_chains"]),
+        times = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            S = relax.structure_factor()
+            times.append(1e3 * (time.perf_counter() - t0))
+        sq = {"ms_first": times[0], "ms": times[1], "modes": int(S.size), "chains": int(wl["n_chains"]),
               "includes": "state to FP64 rows, batched real-to-complex cuFFT, mean |u_q|^2 over chains, "
-                          "copy to host (work area allocated and freed in the call)"}
+                          "copy to host (work area allocated and freed in the call); the first call also "
+                          "builds the plan"}
 
     # ---- FP64 plain path on the same chains (the comparison the metric names) ----
     fp64 = None
@@ -474,7 +532,8 @@ def main() -> None:
                        "l2": (f"inputs larger than L2 ({state_gib:.2f} GiB state), no flush" if state_gib > 0.129
                               else f"state of {state_gib * 1024:.1f} MiB fits in L2 (not a bandwidth measurement)"),
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
-            "roofline": roofline, "fp64_path": fp64, "cpu_baseline": cpu, "e2e": e2e, "structure_factor": sq,
+            "roofline": roofline, "horizon": horizon, "fp64_path": fp64, "cpu_baseline": cpu, "e2e": e2e,
+            "structure_factor": sq,
             "gpu_launches": st["launches"], "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -130,9 +130,10 @@ int qew_set_samples(qew_handle h, const uint32_t* s);
  * `K` Euler steps per HBM round trip (temporal-block depth, 1 <= K <= w / 4 for the narrowest
  * tile w in use),
  * `tiles_per_cta` warp tiles per thread block (1, 2, 4 or 8).
- * Passing 0 for all three asks for the autotuner: it times candidate shapes on the handle's own
- * chains, without changing their state, as soon as they are at least 1024 Euler steps past the
- * flat start (the best shape changes while the rate of cell crossings decays after the flat
+ * Passing 0 for all three asks for the autotuner: it times candidate shapes (every supported tile
+ * width, K in {4, 8, 16, 32} up to the limit above, 1, 2 or 4 tiles per block) on the handle's
+ * own chains, without changing their state, as soon as they are at least 1024 Euler steps past
+ * the flat start (the best shape changes while the rate of cell crossings decays after the flat
  * start); until then the default shape is used.
  * Results never depend on the shape beyond FP32 rounding order, which is identical: each
  * site's arithmetic is the same for every shape.
@@ -262,6 +263,8 @@ int qew_get_stats(qew_handle h, int64_t* launches, int64_t* fused_launches, doub
  *   cell, off  DEVICE pointers, batch * L elements each, chain c at offset c * L: the integer cell
  *              n_i and the FP32 offset d_i in [0, 1) of u_i = n_i + d_i (the layout that
  *              qew_get_cells / qew_get_state describe).  Chain c has sample index s = c.
+ *              Cells are summed relative to the first cell of each 256-site tile, in FP32: the
+ *              sums keep their accuracy while cells inside a tile differ by less than 2^24.
  *   f, disorder_kind, seed  as in qew_create; the pinning force is regenerated from them.
  *   stream     cudaStream_t to run on (NULL: legacy default stream); synchronised before return.
  *   v_out, ubar_out, w2_out  HOST pointers to `batch` doubles each, or NULL.

@@ -559,13 +559,20 @@ int autotune(qew_ctx* h)
         }
     }
     const int S_all[] = {7, 15, 23, 31, 39};
-    const int K_all[] = {8, 16, 32};
+    const int K_all[] = {4, 8, 16, 32};
     const int T_all[] = {1, 2, 4};
     float best = 1e30f;
     int bS = h->S, bK = h->K, bT = h->tpc;
-    cudaEvent_t e0, e1;
-    QEW_CUDA(h, cudaEventCreate(&e0), "creating tuning events");
-    QEW_CUDA(h, cudaEventCreate(&e1), "creating tuning events");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess)
+        ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        if (e0)
+            cudaEventDestroy(e0);
+        return cuda_fail(h, ce, "creating tuning events");
+    }
+    int rc = QEW_OK;
     for (int S : S_all) {
         // a requested width that no kind present runs would repeat a narrower candidate
         bool used = false;
@@ -583,26 +590,29 @@ int autotune(qew_ctx* h)
                 h->S = S;
                 h->K = K;
                 h->tpc = T;
-                int rc = build_layout(h);
-                if (rc != QEW_OK)
-                    return rc;
+                rc = build_layout(h);
                 // best of four timed repetitions (after one untimed), each two launches long, so a
                 // shape wins by its throughput rather than by the noise of a single launch
                 float ms_best = 1e30f;
-                for (int rep = 0; rep < 5; ++rep) {
+                for (int rep = 0; rep < 5 && rc == QEW_OK; ++rep) {
                     cudaEventRecord(e0, h->stream);
-                    for (int l = 0; l < 2; ++l) {
+                    for (int l = 0; l < 2 && rc == QEW_OK; ++l)
                         rc = launch_split_all(h, K, 0, h->sp[h->cur], h->sp[h->cur ^ 1]);
-                        if (rc != QEW_OK)
-                            return rc;
-                    }
+                    if (rc != QEW_OK)
+                        break;
                     cudaEventRecord(e1, h->stream);
-                    QEW_CUDA(h, cudaEventSynchronize(e1), "timing a tuning candidate");
+                    ce = cudaEventSynchronize(e1);
+                    if (ce != cudaSuccess) {
+                        rc = cuda_fail(h, ce, "timing a tuning candidate");
+                        break;
+                    }
                     float ms = 0;
                     cudaEventElapsedTime(&ms, e0, e1);
                     if (rep > 0)
                         ms_best = std::min(ms_best, 0.5f * ms);
                 }
+                if (rc != QEW_OK)
+                    break;
                 const float per = ms_best / static_cast<float>(K);
                 if (per < best) {
                     best = per;
@@ -611,10 +621,16 @@ int autotune(qew_ctx* h)
                     bT = T;
                 }
             }
+            if (rc != QEW_OK)
+                break;
         }
+        if (rc != QEW_OK)
+            break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rc != QEW_OK)
+        return rc;
     h->S = bS;
     h->K = bK;
     h->tpc = bT;

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kNaWarps * 32) na_tile_sums(const int32_t* __r
             g = fmaf(d, fmaf(d, C, B), A);
         }
         sF += g - f;
-        const float y = qew::small_int_to_float(n - nref) + d;
+        const float y = static_cast<float>(n - nref) + d;   // the cell difference is exact below 2^24
         sy += y;
         syy = fmaf(y, y, syy);
         ++cnt;

@@ -1,5 +1,5 @@
 """The allocation-free observation entry point, qew_observe_state_noalloc, checked against the
-handle-based qew_observe_ex on the same state.
+handle-based qew_observe_ex on the same state, and against the CPU oracle.
 
 Some callers cannot let a library call cudaMalloc.  One example is a framework whose caching
 allocator already holds the GPU's memory, where an allocation behind its back can fail or
@@ -9,8 +9,11 @@ observables of a state that the caller keeps in device memory, using a fixed scr
 inside the library instead of allocating.  Here a handle relaxes a batch of chains and reports
 v, ubar and w2 at its last observation step.  The same state, copied into caller-owned device
 buffers, goes through the allocation-free entry point twice in a row.  Both calls must agree
-with the handle within the tolerances the parity tests use for these observables.  Oversized
-inputs must be rejected.
+with the handle within the tolerances the parity tests use for these observables, and with the
+oracle's v, ubar and w2 of that state (Eqs. 3-5, FP64 and the exact disorder values) within
+what the FP32 disorder values and sums allow.  Every disorder kind is covered, and a batch of
+more than 64 chains, which the entry point copies back in several chunks.  Oversized inputs must
+be rejected.
 """
 import ctypes
 
@@ -26,8 +29,9 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-@pytest.mark.parametrize("kind,f,L,batch", [(0, 0.72057, 5000, 3), (1, 0.90749, 3001, 2), (2, 0.4, 700, 1)])
-def test_noalloc_matches_observe(kind, f, L, batch):
+@pytest.mark.parametrize("kind,f,L,batch", [(0, 0.72057, 5000, 3), (1, 0.90749, 3001, 2), (2, 0.4, 700, 1),
+                                            (3, 1.5652, 2049, 2), (4, 1.9, 1500, 2), (0, 0.9, 300, 70)])
+def test_noalloc_matches_observe(orc, kind, f, L, batch):
     torch = pytest.importorskip("torch")
     import paper_1211_7275_gb300 as q
     lib = q.load()
@@ -37,6 +41,7 @@ def test_noalloc_matches_observe(kind, f, L, batch):
         u, _ = r.state()
         cells = r.cells()
     off = (u - cells).astype(np.float32)   # exact: u = n + d with d stored in FP32
+    ref = orc.run([L] * batch, f, 0.1, kind, SEED, [0], u0=u)
     cell_d = torch.from_numpy(np.ascontiguousarray(cells)).cuda()
     off_d = torch.from_numpy(np.ascontiguousarray(off)).cuda()
     stream = torch.cuda.current_stream()
@@ -51,6 +56,11 @@ def test_noalloc_matches_observe(kind, f, L, batch):
         np.testing.assert_allclose(v, obs["v"][-1], rtol=0, atol=2e-4)
         np.testing.assert_allclose(ub, obs["ubar"][-1], rtol=0, atol=2e-5)
         np.testing.assert_allclose(w2, obs["w2"][-1], rtol=1e-4, atol=1e-6)
+        # the oracle on the same state: FP32 disorder values (relative error 6e-7 for the Gaussian
+        # kinds, cubic coefficients up to ~20) and FP32 tile sums
+        np.testing.assert_allclose(v, ref["v"][0], rtol=0, atol=2e-5)
+        np.testing.assert_allclose(ub, ref["ubar"][0], rtol=0, atol=2e-6 * max(1.0, np.abs(ub).max()))
+        np.testing.assert_allclose(w2, ref["w2"][0], rtol=2e-5, atol=1e-8)
 
 
 def test_noalloc_rejects_oversized_input():
