@@ -154,7 +154,12 @@ int qew_advance(qew_handle h, int64_t n_steps);
  * w2_out[k * n_chains + c] = w2 of chain c at step steps[k].  Either output may be NULL.
  * n_times == 0 is a no-op.  Returns after the results are in host memory.  On return the
  * chains are at step steps[n_times - 1].  QEW_ENONFINITE if an observable is NaN/Inf (the
- * outputs are still written).  The schedule's launches (fused segments, reductions and the copy
+ * outputs are still written).  QEW_ESTATE if, at an observation of the FP32-split state,
+ * neighbouring sites differ by 2^12 cells or more: outside that range the fused kernel's cell
+ * arithmetic is no longer exact, so the state is reported as invalid instead of silently wrong
+ * (the Euler map with dt < 0.5 grows a neighbour difference by at most 2 dt max|F_p| per step, so
+ * a line started within the range stays in it for thousands of steps at least; physical lines stay
+ * far inside it).  The schedule's launches (fused segments, reductions and the copy
  * to the host) are captured into a CUDA graph the first time and replayed whenever the same
  * schedule is observed again from the same step (e.g. after qew_reset); not while statistics
  * are enabled, and not for schedules needing more than 20000 launches.

@@ -522,7 +522,9 @@ int run_to(qew_ctx* h, int64_t target, double* obs)
         if (obs) {
             QEW_CUDA(h, reduce_chains(h->d_chains, h->n_chains, h->d_partial, h->d_shift, obs, 1, h->stream),
                      "launching the observable reduction");
-            h->n_launches += 1;
+            QEW_CUDA(h, split_range_guard(h->d_chains, h->d_btiles, h->n_btiles, kBlockTile, h->sp[h->cur].cell,
+                                          h->d_error, h->stream), "launching the range guard");
+            h->n_launches += 2;
         }
     } else {
         while (h->step < target) {
@@ -741,13 +743,17 @@ int check_handle(qew_handle h)
     return QEW_OK;
 }
 
-// A kernel whose bounded wait on a bulk copy gave up leaves 1 in d_error; report it once.
+// A kernel whose bounded wait on a bulk copy gave up leaves 1 in d_error; one whose range guard
+// found neighbouring cells 2^12 or more apart leaves 2.  Report it once.
 int check_device_error(qew_ctx* h)
 {
     int32_t flag = 0;
     QEW_CUDA(h, cudaMemcpy(&flag, h->d_error, sizeof(flag), cudaMemcpyDeviceToHost), "reading the error flag");
     if (flag) {
         cudaMemset(h->d_error, 0, sizeof(int32_t));
+        if (flag == 2)
+            return fail(h, QEW_ESTATE, "neighbouring displacements reached 2^12 cells, outside the range the "
+                                       "FP32-split kernel represents exactly; the state is no longer valid");
         return fail(h, QEW_ETIMEOUT, "a bounded wait for a bulk copy gave up; the state is no longer valid");
     }
     return QEW_OK;

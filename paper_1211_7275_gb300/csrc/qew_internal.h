@@ -43,7 +43,7 @@ struct SplitLaunch {
     const double* shift;     // per-chain reference cell c of the sums
     double* partial;         // [n_tiles_total][3]: sum F, sum (u - c), sum (u - c)^2
     unsigned long long* crossings;  // if not null: cell crossings are added here
-    int32_t* error;          // set to 1 if a bounded wait on a bulk copy gave up
+    int32_t* error;          // 1: a bounded wait on a bulk copy gave up; 2: neighbouring cells 2^12 apart
     PhiloxKeys keys;         // round keys of `seed`
 };
 
@@ -56,6 +56,10 @@ cudaError_t split_init(const ChainDesc* chains, int32_t n_chains, const TileDesc
                        cudaStream_t stream);
 cudaError_t split_to_f64(const ChainDesc* chains, const TileDesc* tiles, int32_t n_tiles, int32_t w_tile,
                          SplitState st, double* u_out, int32_t* cells_out, cudaStream_t stream);
+// Sets *error to 2 if neighbouring cells of the FP32-split state differ by 2^12 or more (the range
+// in which the fused kernel's cell arithmetic is exact).
+cudaError_t split_range_guard(const ChainDesc* chains, const TileDesc* tiles, int32_t n_tiles, int32_t w_tile,
+                              const int32_t* cell, int32_t* error, cudaStream_t stream);
 
 struct F64Launch {
     const TileDesc* tiles;   // block tiles of w_tile sites

@@ -514,3 +514,28 @@ def test_full_size_uneven_256(qew, orc):
     f = base * (1.0 + sweep_offsets(256))
     chains = [int(np.argmin(L)), int(np.argmax(L)), 5, 100, 255]
     _sampled_sites_check(qew, orc, L, f, kinds, 256, 600, 2, chains_to_check=chains)
+
+
+def test_steep_state_within_the_exact_range(qew, orc):
+    """A valid but extreme state: a triangle wave rising by 4000 cells per site (below the 2^12
+    limit on neighbouring displacements that qew_set_state enforces), so a tile window spans
+    millions of cells.  The kernel's range guard (at observations) checks the neighbour
+    differences of such windows and must not raise; the cells relative to a tile's reference stay
+    exact floats (below 2^24), and per site the FP32-split state follows the oracle over 100 steps
+    to FP32 precision relative to u (the Laplacian moves the peaks by hundreds of cells per step)."""
+    L, f, n = 3000, 0.5, 100
+    i = np.arange(L)
+    tri = np.minimum(i % 600, 600 - i % 600)
+    u0 = 4000.0 * tri + 0.25
+    steps = np.array([0, 1, 10, n])
+    obs, u, _ = gpu_run(qew, L, f, RF, steps, FP32, u0=u0)
+    ref = orc.run(L, f, 0.1, RF, SEED, steps, u0=u0, want_state=True)
+    # FP32 keeps the Laplacian's neighbour differences of ~4000 cells to 2^-24 relative, so the
+    # per-site error scales with the local slope, not with 1e-4 cells
+    rel = np.abs(u - ref["u"]) / np.maximum(1.0, np.abs(ref["u"]))
+    assert rel.max() <= 1e-7, rel.max()
+    # the fused sums are FP32 relative to a cell of each tile: error at most gamma_40 * D with D the
+    # spread of a tile window (here 992 * 4000 cells; see tests/test_gpu_observables.py)
+    D = 992 * 4000.0 + 1.0
+    gamma = 40 * 2.0 ** -24 / (1 - 40 * 2.0 ** -24)
+    assert np.all(np.abs(obs["ubar"][:, 0] - ref["ubar"][:, 0]) <= gamma * D)
