@@ -144,7 +144,9 @@ int qew_set_tuning(qew_handle h, int32_t tile_w, int32_t K, int32_t tiles_per_ct
  * tile among the batch's kinds. */
 int qew_get_tuning(qew_handle h, int32_t* tile_w, int32_t* K, int32_t* tiles_per_cta);
 
-/* qew_advance -- n_steps >= 0 Euler steps of every chain. */
+/* qew_advance -- n_steps >= 0 Euler steps of every chain.  Asynchronous: the work is queued on the
+ * handle's stream.  A range violation of the FP32-split state found at its end (see qew_observe)
+ * is reported by the next call that reads results (qew_observe, qew_get_state, qew_get_cells). */
 int qew_advance(qew_handle h, int64_t n_steps);
 
 /*
@@ -154,12 +156,12 @@ int qew_advance(qew_handle h, int64_t n_steps);
  * w2_out[k * n_chains + c] = w2 of chain c at step steps[k].  Either output may be NULL.
  * n_times == 0 is a no-op.  Returns after the results are in host memory.  On return the
  * chains are at step steps[n_times - 1].  QEW_ENONFINITE if an observable is NaN/Inf (the
- * outputs are still written).  QEW_ESTATE if, at an observation of the FP32-split state,
- * neighbouring sites differ by 2^12 cells or more: outside that range the fused kernel's cell
- * arithmetic is no longer exact, so the state is reported as invalid instead of silently wrong
- * (the Euler map with dt < 0.5 grows a neighbour difference by at most 2 dt max|F_p| per step, so
- * a line started within the range stays in it for thousands of steps at least; physical lines stay
- * far inside it).  The schedule's launches (fused segments, reductions and the copy
+ * outputs are still written).  QEW_ESTATE if, at the end of the call (or of an earlier
+ * qew_advance), neighbouring sites of the FP32-split state differ by 2^12 cells or more: outside
+ * that range the fused kernel's cell arithmetic is no longer exact, so the state is reported as
+ * invalid instead of silently wrong (the Euler map with dt < 0.5 grows a neighbour difference by
+ * at most 2 dt max|F_p| per step, so a line started within the range stays in it for thousands of
+ * steps at least; physical lines stay far inside it).  The schedule's launches (fused segments, reductions and the copy
  * to the host) are captured into a CUDA graph the first time and replayed whenever the same
  * schedule is observed again from the same step (e.g. after qew_reset); not while statistics
  * are enabled, and not for schedules needing more than 20000 launches.

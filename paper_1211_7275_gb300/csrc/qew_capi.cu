@@ -483,6 +483,18 @@ F64Launch f64_args(qew_ctx* h)
 
 int autotune(qew_ctx* h);
 
+// Range check of the FP32-split state (neighbouring cells less than 2^12 apart), at the end of every
+// call that advances the chains; a violation is reported by the next check_device_error.
+int guard_range(qew_ctx* h)
+{
+    if (h->precision != QEW_FP32_SPLIT)
+        return QEW_OK;
+    QEW_CUDA(h, split_range_guard(h->d_chains, h->n_chains, *std::max_element(h->L.begin(), h->L.end()),
+                                  h->sp[h->cur].cell, h->d_error, h->stream), "launching the range guard");
+    h->n_launches += 1;
+    return QEW_OK;
+}
+
 // The autotuner times candidate shapes only once the chains are this many steps past the flat
 // start.  The best shape changes while the crossing rate decays: measured on 4 x 2^25 random-
 // field chains at f_c, 736-site tiles are 4% faster than 992-site ones over steps 0-256, equal
@@ -522,9 +534,7 @@ int run_to(qew_ctx* h, int64_t target, double* obs)
         if (obs) {
             QEW_CUDA(h, reduce_chains(h->d_chains, h->n_chains, h->d_partial, h->d_shift, obs, 1, h->stream),
                      "launching the observable reduction");
-            QEW_CUDA(h, split_range_guard(h->d_chains, h->d_btiles, h->n_btiles, kBlockTile, h->sp[h->cur].cell,
-                                          h->d_error, h->stream), "launching the range guard");
-            h->n_launches += 2;
+            h->n_launches += 1;
         }
     } else {
         while (h->step < target) {
@@ -838,6 +848,8 @@ int observe_impl(qew_ctx* h, const int64_t* steps, int32_t n_times, double* v_ou
         }
         for (int32_t k = 0; k < n_times && rc == QEW_OK; ++k)
             rc = run_to(h, steps[k], h->d_obs + per * k);
+        if (rc == QEW_OK)
+            rc = guard_range(h);
         cudaError_t ce = cudaSuccess;
         if (rc == QEW_OK)
             ce = cudaMemcpyAsync(h->h_obs, h->d_obs, per * n_times * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -1115,6 +1127,8 @@ int qew_advance(qew_handle h, int64_t n_steps)
         return fail(h, QEW_EINVAL, "n_steps must be >= 0");
     DeviceGuard g(h->device);
     int rc = run_to(h, h->step + n_steps, nullptr);
+    if (rc == QEW_OK && n_steps > 0)
+        rc = guard_range(h);
     if (rc == QEW_OK) {
         cudaError_t e = cudaPeekAtLastError();
         if (e != cudaSuccess)

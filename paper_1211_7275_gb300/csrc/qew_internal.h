@@ -57,9 +57,9 @@ cudaError_t split_init(const ChainDesc* chains, int32_t n_chains, const TileDesc
 cudaError_t split_to_f64(const ChainDesc* chains, const TileDesc* tiles, int32_t n_tiles, int32_t w_tile,
                          SplitState st, double* u_out, int32_t* cells_out, cudaStream_t stream);
 // Sets *error to 2 if neighbouring cells of the FP32-split state differ by 2^12 or more (the range
-// in which the fused kernel's cell arithmetic is exact).
-cudaError_t split_range_guard(const ChainDesc* chains, const TileDesc* tiles, int32_t n_tiles, int32_t w_tile,
-                              const int32_t* cell, int32_t* error, cudaStream_t stream);
+// in which the fused kernel's cell arithmetic is exact); max_L is the longest chain.
+cudaError_t split_range_guard(const ChainDesc* chains, int32_t n_chains, int64_t max_L, const int32_t* cell,
+                              int32_t* error, cudaStream_t stream);
 
 struct F64Launch {
     const TileDesc* tiles;   // block tiles of w_tile sites

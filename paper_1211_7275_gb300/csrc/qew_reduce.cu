@@ -1,4 +1,5 @@
-// qew_reduce.cu -- second pass of the checkpoint reductions, and the generator diagnostics.
+// qew_reduce.cu -- second pass of the checkpoint reductions, the range guard of the FP32-split
+// state at observations, and the generator diagnostics.
 //
 // Observables (arXiv:1211.7275, Sec. II, Eqs. 3-5) per chain, from the per-tile partial sums
 // written by the step kernels: sum F_p, S1 = sum (u - c) and S2 = sum (u - c)^2, c the chain's
@@ -7,6 +8,8 @@
 // next, so S1 / L stays of the order of the displacement between observations and the
 // one-pass variance keeps its precision.  One block per chain sums its partials in a fixed
 // order, so results are bitwise reproducible from run to run.
+#include <algorithm>
+
 #include "qew_internal.h"
 #include "qew_tma.cuh"
 
@@ -92,7 +95,45 @@ __global__ void bounded_wait_probe(int32_t* error, int limit)
         atomicExch(error, 1);
 }
 
+// Range guard of the FP32-split state, run at every observation: the fused kernel carries cells as
+// exact small floats relative to a cell of its tile window and (compact layout) decodes a step's
+// move from 16 bits of the cell.  Both hold while neighbouring cells differ by less than 2^12: then
+// no Euler step moves a site by 2^15 cells (the Euler map grows a neighbour difference by at most
+// 2 dt max|F_p| per step) and a 992-site window spans less than 2^22 cells.  A violation sets the
+// error flag to 2.  Blocks (x, y) stride over the sites of chains y, y + gridDim.y, ...; the
+// chain descriptor is read once per chain, so a thread's loads are independent of one another.
+__global__ void __launch_bounds__(256) split_range_guard_kernel(const ChainDesc* chains, int32_t n_chains,
+                                                               const int32_t* __restrict__ cell, int32_t* error)
+{
+    bool bad = false;
+    for (int32_t c = blockIdx.y; c < n_chains; c += gridDim.y) {
+        const ChainDesc ch = chains[c];
+        const int32_t* cc = cell + ch.offset;
+        const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+#pragma unroll 4
+        for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < ch.L; i += stride) {
+            const int64_t j = (i + 1 == ch.L) ? 0 : i + 1;   // 64-bit: chains reach 2^31 - 1 sites
+            const int64_t dn = static_cast<int64_t>(__ldg(cc + j)) - __ldg(cc + i);
+            bad = bad || dn >= 4096 || dn <= -4096;
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0)
+        atomicExch(error, 2);
+}
+
 }  // namespace
+
+cudaError_t split_range_guard(const ChainDesc* chains, int32_t n_chains, int64_t max_L, const int32_t* cell,
+                              int32_t* error, cudaStream_t stream)
+{
+    if (n_chains == 0)
+        return cudaSuccess;
+    // about 16 sites per thread along x, at most 1024 blocks per chain
+    const int64_t bx = std::min<int64_t>(std::max<int64_t>((max_L + 256 * 16 - 1) / (256 * 16), 1), 1024);
+    const dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(std::min<int32_t>(n_chains, 65535)));
+    split_range_guard_kernel<<<grid, 256, 0, stream>>>(chains, n_chains, cell, error);
+    return cudaGetLastError();
+}
 
 cudaError_t bounded_wait_selftest(int32_t* d_error, int spin_limit, cudaStream_t stream)
 {

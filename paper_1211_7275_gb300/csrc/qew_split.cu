@@ -31,7 +31,6 @@
 // evaluated 32 lanes at a time and
 // written straight into the shared-memory cache of the requesting sites; the direction of each
 // move is recovered from the cell the cache was drawn for, kept per site in shared memory.
-#include <algorithm>
 #include <cstdio>
 #include <mutex>
 #include <type_traits>
@@ -633,49 +632,7 @@ __global__ void split_to_f64_kernel(const ChainDesc* chains, const TileDesc* til
     }
 }
 
-// Range guard of the FP32-split state, run at every observation: the fused kernel carries cells as
-// exact small floats relative to a cell of its tile window and (compact layout) decodes a step's
-// move from 16 bits of the cell.  Both hold while neighbouring cells differ by less than 2^12: then
-// no Euler step moves a site by 2^15 cells (the Euler map grows a neighbour difference by at most
-// 2 dt max|F_p| per step) and a 992-site window spans less than 2^22 cells.  A violation sets the
-// error flag to 2.  One thread per site, block tiles of w_tile sites.
-__global__ void split_range_guard_kernel(const ChainDesc* chains, const TileDesc* tiles, int32_t n_tiles,
-                                         int32_t w_tile, const int32_t* __restrict__ cell, int32_t* error)
-{
-    bool bad = false;
-    for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const TileDesc td = tiles[t];
-        const ChainDesc ch = chains[td.chain];
-        for (int x = threadIdx.x; x < w_tile; x += blockDim.x) {
-            const int32_t i = td.start + x;
-            if (i >= ch.L)
-                break;
-            const int32_t j = (i + 1 == ch.L) ? 0 : i + 1;
-            const int64_t dn = static_cast<int64_t>(__ldg(cell + ch.offset + j)) - __ldg(cell + ch.offset + i);
-            bad = bad || dn >= 4096 || dn <= -4096;
-        }
-    }
-    if (__syncthreads_or(bad) && threadIdx.x == 0)
-        atomicExch(error, 2);
-}
-
 }  // namespace
-
-cudaError_t split_range_guard(const ChainDesc* chains, const TileDesc* tiles, int32_t n_tiles, int32_t w_tile,
-                              const int32_t* cell, int32_t* error, cudaStream_t stream)
-{
-    if (n_tiles == 0)
-        return cudaSuccess;
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess)
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess)
-        return e;
-    const int grid = static_cast<int>(std::min<int64_t>(n_tiles, static_cast<int64_t>(sms) * 8));
-    split_range_guard_kernel<<<grid, 256, 0, stream>>>(chains, tiles, n_tiles, w_tile, cell, error);
-    return cudaGetLastError();
-}
 
 bool split_supported(int kind, int S)
 {

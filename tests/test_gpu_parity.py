@@ -519,7 +519,7 @@ def test_full_size_uneven_256(qew, orc):
 def test_steep_state_within_the_exact_range(qew, orc):
     """A valid but extreme state: a triangle wave rising by 4000 cells per site (below the 2^12
     limit on neighbouring displacements that qew_set_state enforces), so a tile window spans
-    millions of cells.  The kernel's range guard (at observations) checks the neighbour
+    millions of cells.  The range guard at the end of each call checks the neighbour
     differences of such windows and must not raise; the cells relative to a tile's reference stay
     exact floats (below 2^24), and per site the FP32-split state follows the oracle over 100 steps
     to FP32 precision relative to u (the Laplacian moves the peaks by hundreds of cells per step)."""
