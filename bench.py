@@ -64,6 +64,9 @@ def parse():
                    help="Euler steps of the one relaxation timed at the workload's own horizon, outside the timed "
                         "loop (default: the preset's n_steps, 2^20 for rf_4x2^25; 0: skip)")
     p.add_argument("--horizon-obs", type=int, default=None, help="observations of that relaxation (default: the preset's)")
+    p.add_argument("--others", default="rb_1024x2^16,uneven_256,rbg_linear_4x2^25,none_16x2^20",
+                   help="presets whose fused kernels get a short roofline measurement beside the main line "
+                        "(comma-separated; empty: none)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -290,6 +293,51 @@ def run_reference(args, rank: int, world: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+# Launch shapes the autotuner picks for the other presets on a GB300 (their own relaxations, at
+# step 1024); the short measurement below uses them directly instead of tuning again.
+OTHER_SHAPES = {"rb_1024x2^16": (480, 16, 1), "uneven_256": (736, 32, 1), "rbg_linear_4x2^25": (480, 8, 1),
+                "none_16x2^20": (736, 32, 2), "rf_16x2^20": (992, 32, 2), "rf_4x2^25": (992, 32, 2)}
+
+
+def other_kernel(q, name: str, stream, sms: int, clk_mhz: float, n_steps: int = 1024) -> dict:
+    """Site-updates/s and roofline fraction of the fused kernel on another preset: one relaxation of
+    ``n_steps`` from the flat start in the preset's tuned shape (after one untimed run), fused
+    observations at 12 log-spaced steps, device time from CUDA events on the library's stream."""
+    import torch
+    wl = workload(name, 0)
+    sched = W.log_spaced_steps(n_steps, 12)
+    r = q.Relaxation(wl["L"], wl["f"], wl["kind"], dt=wl["dt"], seed=wl["seed"], precision=q.FP32_SPLIT,
+                     batch=wl["batch"], stream=stream)
+    try:
+        r.set_tuning(*OTHER_SHAPES[name])
+        r.observe(sched)
+        r.reset()
+        r.enable_stats(True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r.observe(sched)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = r.stats()
+        n_sites = r.n_sites
+    finally:
+        r.close()
+    ms = e0.elapsed_time(e1)
+    kinds = np.broadcast_to(np.asarray(wl["kind"]), (wl["n_chains"],))
+    sites = np.broadcast_to(np.asarray(wl["L"], dtype=np.float64), (wl["n_chains"],))
+    wk = {int(k): float(sites[kinds == k].sum() / sites.sum()) for k in set(kinds.tolist())}
+    rx = st["crossings"] / max(1, st["site_updates"])
+    ops = sum(w * (OPS_BASE[k] + OPS_PER_CROSSING[k] * rx) for k, w in wk.items())
+    peak = sms * LANES_PER_SM * clk_mhz * 1e6 / 1e12
+    ach = ops * st["site_updates"] / (st["fused_ms"] / 1e3) / 1e12 if st["fused_ms"] > 0 else None
+    return {"value": n_sites * n_steps / (ms / 1e3), "unit": UNIT, "relax_steps": n_steps,
+            "tuning": dict(zip(("tile_w", "K", "tiles_per_cta"), OTHER_SHAPES[name])),
+            "crossings_per_site_update": rx, "ops_per_site_update": ops,
+            "roofline_frac": (ach / peak) if ach else None, "fused_share": st["fused_ms"] / ms if ms > 0 else None}
+
+
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
@@ -448,6 +496,11 @@ def main() -> None:
             horizon["early"] = leg_fields(legs[0][0], legs[0][1], split)
             horizon["late"] = leg_fields(legs[1][0], legs[1][1], h_steps - split)
 
+    # ---- the other presets' fused kernels: a short relaxation each, outside the timed region ----
+    others = {}
+    for name in [x for x in args.others.split(",") if x and x != wl["name"]]:
+        others[name] = other_kernel(q, name, stream, sms, (clocks or {}).get("sm_mhz") or clk)
+
     # ---- structure factor (Eq. 6) of the relaxed chains, outside the timed region: the first call
     # builds the cuFFT plan; the second shows the steady state ----
     sq = None
@@ -532,7 +585,7 @@ def main() -> None:
                        "l2": (f"inputs larger than L2 ({state_gib:.2f} GiB state), no flush" if state_gib > 0.129
                               else f"state of {state_gib * 1024:.1f} MiB fits in L2 (not a bandwidth measurement)"),
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
-            "roofline": roofline, "horizon": horizon, "fp64_path": fp64, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "horizon": horizon, "other_kernels": others or None, "fp64_path": fp64, "cpu_baseline": cpu, "e2e": e2e,
             "structure_factor": sq,
             "gpu_launches": st["launches"], "clocks": clocks,
         }
