@@ -539,3 +539,25 @@ def test_steep_state_within_the_exact_range(qew, orc):
     D = 992 * 4000.0 + 1.0
     gamma = 40 * 2.0 ** -24 / (1 - 40 * 2.0 ** -24)
     assert np.all(np.abs(obs["ubar"][:, 0] - ref["ubar"][:, 0]) <= gamma * D)
+
+
+def test_range_guard_reports_a_state_outside_the_exact_range(qew, orc):
+    """A triangle wave rising 4095 cells per site is accepted (neighbours below 2^12 apart), but
+    the pinning force pushes some neighbour differences to 4097-4098 cells within 50 steps (the
+    oracle shows hundreds of such sites).  The range check at the end of the call must then report
+    QEW_ESTATE instead of returning the observables; the next call starts clean."""
+    L = 3000
+    i = np.arange(L)
+    tri = np.minimum(i % 600, 600 - i % 600)
+    u0 = 4095.0 * tri + 0.25
+    ref = orc.run(L, 0.5, 0.1, RF, SEED, [50], u0=u0, want_state=True)["u"]
+    cells = np.floor(ref)
+    assert np.abs(np.diff(np.r_[cells, cells[0]])).max() >= 4097   # the oracle crosses the bound
+    with qew.Relaxation(L, 0.5, RF, dt=0.1, seed=SEED, precision=FP32) as r:
+        r.set_state(u0)
+        with pytest.raises(qew.QewError) as ei:
+            r.observe([50])
+        assert ei.value.code == -6 and b"2^12" in str(ei.value).encode()
+        r.set_state(np.zeros(L))            # a valid state: the flag was cleared
+        obs = r.observe([0, 10])
+        assert np.all(np.isfinite(obs["v"]))
