@@ -561,3 +561,44 @@ def test_range_guard_reports_a_state_outside_the_exact_range(qew, orc):
         r.set_state(np.zeros(L))            # a valid state: the flag was cleared
         obs = r.observe([0, 10])
         assert np.all(np.isfinite(obs["v"]))
+
+
+def test_creation_and_state_argument_errors(qew):
+    """Every precondition of qew_create / qew_set_state is checked on the host and reported as
+    QEW_EINVAL (-1); a batch larger than the device's memory is QEW_ENOMEM (-2), with nothing left
+    allocated."""
+    bad = [dict(L=0, f=1.0), dict(L=100, f=float("nan")), dict(L=100, f=4096.0), dict(L=100, f=1.0, dt=0.5),
+           dict(L=100, f=1.0, dt=0.0), dict(L=100, f=1.0, kind=5), dict(L=1 << 31, f=1.0)]
+    for kw in bad:
+        with pytest.raises(qew.QewError) as e:
+            qew.Relaxation(kw.pop("L"), kw.pop("f"), kw.pop("kind", RF), **kw)
+        assert e.value.code == -1, kw
+    with pytest.raises(qew.QewError) as e:   # 2^37 sites: the first state array alone exceeds the GPU
+        qew.Relaxation((1 << 31) - 1, 1.0, RF, batch=64)
+    assert e.value.code == -2
+    with qew.Relaxation(100, 1.0) as r:
+        for u in (np.r_[np.zeros(99), 5000.0], np.full(100, 2.0 ** 30), np.r_[np.zeros(99), np.inf]):
+            with pytest.raises(qew.QewError) as e:
+                r.set_state(u)
+            assert e.value.code == -1
+        obs = r.observe([0, 5])
+        assert np.all(np.isfinite(obs["v"]))
+
+
+def test_sample_indices_select_the_disorder(qew, orc):
+    """qew_set_samples: a chain given sample index s relaxes on the disorder of sample s (the oracle
+    with s), chains given the same index are identical, and resetting to 0..n-1 restores the default."""
+    L, n = 777, 300
+    with qew.Relaxation(L, 1.0, RF, dt=0.1, seed=SEED, precision=FP32, batch=3) as r:
+        r.set_samples([5, 5, 9])
+        r.observe([n])
+        u, _ = r.state()
+        r.set_samples([0, 1, 2])
+        r.observe([n])
+        u0, _ = r.state()
+    u = u.reshape(3, L)
+    assert np.array_equal(u[0], u[1]) and not np.array_equal(u[0], u[2])
+    ref = orc.run([L] * 2, 1.0, 0.1, RF, SEED, [n], s=[5, 9], want_state=True)["u"].reshape(2, L)
+    assert np.max(np.abs(u[0] - ref[0])) <= 1e-4 and np.max(np.abs(u[2] - ref[1])) <= 1e-4
+    ref0 = orc.run([L] * 3, 1.0, 0.1, RF, SEED, [n], want_state=True)["u"]
+    assert np.max(np.abs(u0 - ref0)) <= 1e-4
