@@ -107,3 +107,45 @@ def gamma_drift(t, V, W2, decades: float = 1.0) -> float:
     if np.count_nonzero(sel) < 2:
         raise ValueError("need at least 2 points in the last decade")
     return float(np.polyfit(np.log(t[sel]), np.log(g[sel]), 1)[0])
+
+
+def _main() -> None:
+    """Relax a batch on the GPU and print its STD analysis as one JSON line:
+    python -m paper_1211_7275_gb300.std --L 33554432 --batch 4 --f 1.5652 --kind 3 --steps 1048576"""
+    import argparse
+    import json
+
+    from . import relax
+
+    p = argparse.ArgumentParser(description=_main.__doc__)
+    p.add_argument("--L", type=int, required=True)
+    p.add_argument("--batch", type=int, default=1)
+    p.add_argument("--f", type=float, required=True)
+    p.add_argument("--kind", type=int, default=0, help="0 RF, 1 uniform RB, 3 Gaussian RB linear, 4 Gaussian RB cubic")
+    p.add_argument("--dt", type=float, default=0.1)
+    p.add_argument("--seed", type=int, default=12117275)
+    p.add_argument("--steps", type=int, required=True)
+    p.add_argument("--obs", type=int, default=100, help="log-spaced observation steps")
+    p.add_argument("--tuning", default="auto", help="'auto' or tile_w,K,tiles_per_cta")
+    p.add_argument("--t-mic", type=float, default=2.0, help="lower end of the corrected fits (procedure (a))")
+    a = p.parse_args()
+    k = a.obs
+    steps = sorted({0} | {int(round(a.steps ** (j / (k - 1)))) for j in range(k)} | {a.steps})
+    steps = np.asarray([s for s in steps if s >= 1], dtype=np.int64)
+    with relax.Relaxation(a.L, a.f, a.kind, dt=a.dt, seed=a.seed, batch=a.batch) as r:
+        r.set_tuning(*([0, 0, 0] if a.tuning == "auto" else [int(x) for x in a.tuning.split(",")]))
+        obs = r.observe(steps)
+    t = steps * a.dt
+    V, W2 = obs["v"].mean(1), obs["w2"].mean(1)
+    W = np.sqrt(W2)
+    t0s = [x for x in (10, 30, 100, 300, 1000, 3000, 10000, 25000) if 4 * x <= t[-1]]
+    out = {"L": a.L, "batch": a.batch, "f": a.f, "kind": a.kind, "steps": a.steps, "observations": int(steps.size),
+           "beta_over_nu_z": -fit_corrected(t, V, t_mic=a.t_mic)["e"],
+           "zeta_over_z": fit_corrected(t, W, t_mic=a.t_mic)["e"],
+           "window_t0": t0s, "window_v": window_fits(t, V, t0s).tolist(), "window_w": window_fits(t, W, t0s).tolist(),
+           "gamma_drift_last_decade": gamma_drift(t, V, W2)}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    _main()
