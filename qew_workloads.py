@@ -35,7 +35,10 @@ PRESETS = {
                        n_obs=60),
     "rb_1024x2^16": dict(L=1 << 16, batch=1024, kind=RB, f=0.90749, f_hint=1.0, dt=0.1, n_steps=1 << 18,
                          n_obs=80),
-    "rf_4x2^25": dict(L=1 << 25, batch=4, kind=RF, f=0.72057, f_hint=0.9713, dt=0.1, n_steps=1 << 20,
+    # f_c^L of the 2^25-site chains themselves: the root of the gamma drift (Sec. IV.F) over the
+    # last decade of 2^19-step relaxations of this preset (drift +0.025 at 0.72057, +0.0009 at
+    # 0.7209, -0.020 at 0.7212), run with ``python -m paper_1211_7275_gb300.std`` on a GB300.
+    "rf_4x2^25": dict(L=1 << 25, batch=4, kind=RF, f=0.7209, f_hint=0.9713, dt=0.1, n_steps=1 << 20,
                       n_obs=100),
     "uneven_256": dict(n_chains=256, kind="mixed", dt=0.1, n_steps=1 << 17, n_obs=60),
     # Case 3 at the paper's largest size (Sec. IV.D runs it at L = 2^25 and finds f_c = 1.5652 for
