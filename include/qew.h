@@ -260,6 +260,30 @@ int qew_get_stats(qew_handle h, int64_t* launches, int64_t* fused_launches, doub
                   int64_t* crossings);
 
 /*
+ * qew_critical_force_rf -- the critical force f_c^s and the critical configuration of one random-field
+ * sample periodic in x (L sites) and in u (period M): the largest drive at which a pinned
+ * configuration exists, and that configuration (Sec. III.B; the paper computes them with an exact
+ * algorithm built on Middleton's theorems, which it cites; Sec. IV.A compares them with the
+ * short-time-dynamics threshold).  Host code, FP64, no GPU work.
+ *   R         HOST array [L][M], R[i*M + m] = R(i, m): the sample's force values at the integer
+ *             points (e.g. from qew_disorder_values, QEW_FP64, with n = 0 .. M-1); the force is
+ *             their linear interpolation, periodic in u (Case 4).
+ *   dt        Euler step of the avalanches (0 < dt < 0.5); f_start: a drive at which the flat
+ *             line pins (the search starts from its pinned configuration).
+ *   f_c_out   receives f_c^s; u_c_out (L doubles, or NULL) the critical configuration;
+ *   events_out / dyn_steps_out (or NULL): branch events and Euler steps used.
+ * Method: with the cells fixed the static equation is a linear (periodic tridiagonal) system, so
+ * the pinned configuration is followed exactly while f grows, one cell change at a time; where a
+ * branch ends (the system loses positive definiteness) the line avalanches at fixed f, followed
+ * with the Euler map until it pins again, and f_c^s is the drive at which an avalanche carries
+ * every site a full period M (the motion then repeats forever).
+ * Errors: QEW_EINVAL (sizes, NULL, dt), QEW_ESTATE (the flat line does not pin at f_start, or an
+ * avalanche does not end within the step limit), QEW_ENOMEM; message via qew_last_error(NULL).
+ */
+int qew_critical_force_rf(int64_t L, int64_t M, const double* R, double dt, double f_start, double* f_c_out,
+                          double* u_c_out, int64_t* events_out, int64_t* dyn_steps_out);
+
+/*
  * qew_observe_state_noalloc -- per-chain observables (Eqs. 3-5: v, ubar, w2) of an FP32-split
  * state that the CALLER holds in device memory, computed without allocating any device memory.
  * The paper has no counterpart: this entry point exists for callers that cannot let a library

@@ -58,6 +58,8 @@ SIGNATURES = {
     "qew_get_stats": (ctypes.c_int, [_H, _P, _P, _P, _P, _P]),
     "qew_observe_state_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                                                  ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P]),
+    "qew_critical_force_rf": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_double, ctypes.c_double,
+                                             _P, _P, _P, _P]),
     "qew_selftest_bounded_wait": (ctypes.c_int, [_H, ctypes.c_int32]),
     "qew_last_error": (ctypes.c_char_p, [_H]),
     "qew_destroy": (None, [_H]),

@@ -118,3 +118,26 @@ def test_critical_force_mean_near_the_short_time_threshold(qew):
     fc_std = preset_f("rf_16x2^20")
     print(f"mean f_c^s (512 x 512, 8 samples) = {np.mean(res['f_c']):.4f}, STD f_c^L = {fc_std:.4f}")
     assert abs(np.mean(res["f_c"]) - fc_std) < 0.05 * fc_std
+
+
+def test_exact_critical_force_on_the_device_disorder(qew, orc):
+    """The exact branch-following search (qew_critical_force_rf) on the device generator's FP64
+    force values: for 64 x 64 random-field samples its f_c^s lies inside the GPU bisection's bracket
+    (tol 1e-5), and its critical configuration is the bisection's pinned configuration at the
+    bracket's lower end to within the distance that configuration can still move below f_c^s."""
+    from paper_1211_7275_gb300 import critical
+    res = critical.critical_forces(64, 64, RF, 4, seed=SEED, tol=1e-5)
+    for s in range(4):
+        ex = critical.exact_critical_force(64, 64, s, seed=SEED)
+        assert res["lo"][s] - 1e-9 <= ex["f_c"] <= res["hi"][s] + 1e-9, (s, ex["f_c"], res["lo"][s], res["hi"][s])
+        assert np.max(np.abs(ex["u_c"] - res["u_c"][s])) < 0.05
+
+
+def test_exact_critical_forces_of_512_samples_match_the_short_time_threshold(qew):
+    """Sec. IV.A with the exact search: the mean f_c^s of 16 random-field samples of 512 x 512 lies
+    within 5% of the STD threshold of the 16 x 2^20 preset (finite L and M move it)."""
+    from paper_1211_7275_gb300 import critical
+    from qew_workloads import preset_f
+    fcs = critical.exact_critical_forces(512, 512, 16, seed=SEED)["f_c"]
+    print(f"exact mean f_c^s (512 x 512, 16 samples) = {np.mean(fcs):.5f} +- {np.std(fcs, ddof=1) / 4:.5f}")
+    assert abs(np.mean(fcs) - preset_f("rf_16x2^20")) < 0.05 * preset_f("rf_16x2^20")
