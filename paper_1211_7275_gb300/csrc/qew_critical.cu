@@ -115,7 +115,7 @@ struct Solver {
     double dt;
     std::vector<int64_t> n;    // cells
     std::vector<double> d;     // offsets u - n
-    std::vector<double> dg, rhs, w, ones, p, y1, y2, tmp;
+    std::vector<double> dg, rhs, w, ones, p, y1, y2;
     int64_t events = 0, dyn_steps = 0;
 
     explicit Solver(const Sample& s, double dt_) : smp(s), dt(dt_)
@@ -130,7 +130,6 @@ struct Solver {
         p.resize(L);
         y1.resize(L);
         y2.resize(L);
-        tmp.resize(L);
     }
 
     int64_t nb(int64_t i, int dir) const
@@ -267,6 +266,7 @@ extern "C" int qew_critical_force_rf(int64_t L, int64_t M, const double* R, doub
                                      double* f_c_out, double* u_c_out, int64_t* events_out,
                                      int64_t* dyn_steps_out)
 {
+    // M = 1 would make every site's force constant in u: no stable pinned configuration exists
     if (L < 1 || M < 2 || !R || !f_c_out)
         return (qew::set_last_error("need L >= 1, M >= 2, R and f_c_out"), QEW_EINVAL);
     if (!(dt > 0.0 && dt < 0.5) || !std::isfinite(f_start))
