@@ -296,3 +296,20 @@ def test_bisection_criteria_bracket_the_threshold(qew, criterion):
     up = bisect.drift(1.2 * fc, 1 << 16, 8, RF, 4096, criterion=criterion)
     down = bisect.drift(0.8 * fc, 1 << 16, 8, RF, 4096, criterion=criterion)
     assert up >= 0 > down, (up, down)
+
+
+def test_std_command_line(qew):
+    """python -m paper_1211_7275_gb300.std relaxes a batch on the GPU and prints its short-time
+    analysis as one JSON line (Sec. IV.C-F): finite exponents near the class's values for random-
+    field chains at their threshold."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, "-m", "paper_1211_7275_gb300.std", "--L", "65536", "--batch", "8",
+                          "--f", "0.7206", "--kind", "0", "--steps", "20000", "--obs", "40"],
+                         capture_output=True, text=True, check=True,
+                         cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["observations"] >= 30 and len(d["window_v"]) == len(d["window_t0"])
+    assert 0.08 <= d["beta_over_nu_z"] <= 0.2
+    assert 0.7 <= d["zeta_over_z"] <= 1.0
