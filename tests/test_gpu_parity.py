@@ -124,6 +124,64 @@ def test_split_rb_per_site(qew, orc, L):
     np.testing.assert_allclose(obs["v"], ref["v"], rtol=0, atol=2e-4)
 
 
+@pytest.mark.parametrize("base", [2.0 ** 29 + 0.25, -(2.0 ** 29) - 0.75, -3.5])
+@pytest.mark.parametrize("kind,f", [(RF, 1.0), (RB, 1.9)])
+def test_far_from_zero_per_site(qew, orc, base, kind, f):
+    """A rough line around u = +-2^29 or just below zero.  The disorder counter takes the cell as a
+    two's-complement 32-bit word (negative cells included), the cells stay exact int32, the state
+    read back is n + d, and the observables are summed relative to a chain reference at the
+    line's rounded mean (so w2 of a line at 5e8 keeps its digits).  Per site against the oracle,
+    FP32-split to 1e-4 and FP64 to 1e-6 absolute (1e-15 relative)."""
+    L, steps = 3000, np.array([0, 10, 400])
+    u0 = base + random_state(L, 0.5, seed=21)
+    ref = orc.run(L, f, 0.1, kind, SEED, steps, u0=u0, want_state=True)
+    obs, u, cells = gpu_run(qew, L, f, kind, steps, FP32, u0=u0)
+    _split_check(u, cells, ref["u"])
+    np.testing.assert_allclose(obs["ubar"], ref["ubar"], rtol=0, atol=2e-5)
+    np.testing.assert_allclose(obs["v"], ref["v"], rtol=0, atol=2e-4)
+    np.testing.assert_allclose(obs["w2"], ref["w2"], rtol=1e-4, atol=1e-6)
+    obs64, u64, cells64 = gpu_run(qew, L, f, kind, steps, FP64, u0=u0)
+    assert np.abs(u64 - ref["u"]).max() <= 1e-6
+    assert np.array_equal(cells64, np.floor(u64).astype(np.int64).astype(np.int32))
+    for k in ("v", "ubar", "w2"):
+        np.testing.assert_allclose(obs64[k], ref[k], rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("kind,f", [(RF, 1.0), (RB, 1.9)])
+def test_seed_with_a_high_word(qew, orc, kind, f):
+    """A 64-bit seed whose high word is not zero: both Philox key words (the low and the high 32
+    bits of the seed, reading A1) reach the fused kernel's precomputed key schedule and the FP64
+    kernel.  Per site against the oracle."""
+    seed, L, steps = 0xDEADBEEF12345678, 2048, np.array([0, 25, 600])
+    ref = orc.run(L, f, 0.1, kind, seed, steps, want_state=True)
+    obs, u, cells = gpu_run(qew, L, f, kind, steps, FP32, seed=seed)
+    _split_check(u, cells, ref["u"])
+    np.testing.assert_allclose(obs["v"], ref["v"], rtol=0, atol=2e-4)
+    _, u64, _ = gpu_run(qew, L, f, kind, steps, FP64, seed=seed)
+    assert np.max(np.abs(u64 - ref["u"]) / np.maximum(1.0, np.abs(ref["u"]))) <= 1e-12
+    other = orc.run(L, f, 0.1, kind, seed & 0xFFFFFFFF, steps, want_state=True)
+    assert np.abs(other["u"] - ref["u"]).max() > 1e-2   # the high word changes the disorder
+
+
+@pytest.mark.parametrize("kind,f,dt", [(RF, 1.0, 0.01), (RF, 1.0, 0.25), (RB, 1.9, 0.01), (RB, 1.9, 0.2)])
+def test_other_time_steps(qew, orc, kind, f, dt):
+    """Euler steps other than the paper's dt = 0.1 (Sec. III.B), per site against the oracle in
+    both precisions.  The larger steps are the largest at which the explicit Euler map still
+    forgets a rounding-level difference: the map is monotone only while 1 - 2 dt + dt dF_p/du >= 0,
+    and beyond that it is chaotic.  Measured on the oracle alone (2048 sites, 500 steps), a uniform
+    1e-12 shift of the start ends at 1e-11 for the random field at dt = 0.25 but at 2e-7 at
+    dt = 0.3 and 1.0 at dt = 0.37; for the random bond (steeper spline forces) at 1e-11 at
+    dt = 0.2 and 1.5 at dt = 0.3.  There no two implementations agree per site."""
+    L, steps = 2048, np.array([0, 30, 500])
+    ref = orc.run(L, f, dt, kind, SEED, steps, want_state=True)
+    obs, u, cells = gpu_run(qew, L, f, kind, steps, FP32, dt=dt)
+    _split_check(u, cells, ref["u"])
+    np.testing.assert_allclose(obs["v"], ref["v"], rtol=0, atol=2e-4)
+    obs64, u64, _ = gpu_run(qew, L, f, kind, steps, FP64, dt=dt)
+    assert np.max(np.abs(u64 - ref["u"]) / np.maximum(1.0, np.abs(ref["u"]))) <= 1e-12
+    np.testing.assert_allclose(obs64["v"], ref["v"], rtol=0, atol=1e-11)
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 def test_split_shapes_identical(qew, orc, shape):
     """Every launch shape performs the same per-site arithmetic: states agree bit for bit."""
