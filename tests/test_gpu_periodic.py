@@ -56,6 +56,21 @@ def test_split_per_site(qew, orc, kind, n, M):
     assert np.max(np.abs(u - ref["u"])) <= 1e-4
 
 
+@pytest.mark.parametrize("kind,n", [(RF, 400), (RB, 400), (RBG_CUBIC, 100)])
+def test_negative_cells_per_site(qew, orc, kind, n):
+    """A line far below zero: the node index n mod M must land in [0, M) for negative n as well
+    (the generator is keyed by the wrapped index).  Both GPU paths per site against the oracle
+    (Case 1 over 100 steps, as above)."""
+    L, M, steps = 1500, 7, np.array([0, 9, n])
+    u0 = -1000.3 + random_state(2 * L, 0.5, seed=31)
+    ref = orc.run([L] * 2, FMOVE[kind], 0.1, kind, SEED, steps, u0=u0, want_state=True, period=M)
+    _, u = _run(qew, L, FMOVE[kind], kind, steps, FP32, M, u0=u0)
+    assert np.max(np.abs(u - ref["u"])) <= 1e-4
+    obs, u64 = _run(qew, L, FMOVE[kind], kind, steps, FP64, M, u0=u0)
+    assert np.max(np.abs(u64 - ref["u"]) / np.maximum(1.0, np.abs(ref["u"]))) <= 1e-12
+    np.testing.assert_allclose(obs["v"], ref["v"], rtol=0, atol=1e-11)
+
+
 @pytest.mark.parametrize("kind", [RF, RB, RBG_LINEAR, RBG_CUBIC])
 def test_split_commutes_with_a_shift_by_the_period(qew, kind):
     L, M, steps = 2000, 6, np.array([0, 50, 700])

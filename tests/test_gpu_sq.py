@@ -14,7 +14,7 @@ import math
 import numpy as np
 import pytest
 
-from qew_workloads import SEED, cosine_profile
+from qew_workloads import SEED, cosine_profile, random_state
 
 pytestmark = pytest.mark.gpu
 
@@ -71,6 +71,23 @@ def test_parseval_against_the_fused_width(qew, precision):
         S = r.structure_factor()
     w2 = float(np.mean(obs["w2"][0]))
     assert abs(_parseval(S, L) - w2) <= W2_RTOL[precision] * w2
+
+
+@pytest.mark.parametrize("precision", [FP32, FP64])
+def test_invariant_under_a_lift_of_the_line(qew, precision):
+    """S_q at q != 0 does not see the height of the line (Eq. 6): the same rough lines lifted or
+    lowered by 2^29 cells give the same spectrum bit for bit, because each chain's rows are formed
+    relative to the cell of its first site, exactly in FP64."""
+    L, n_s = 1000, 3
+    u = np.round(random_state(L * n_s, 0.7, seed=51) * 64) / 64   # exact in both layouts
+    spectra = []
+    for lift in (0.0, 2.0 ** 29, -(2.0 ** 29)):
+        with qew.Relaxation(L, 0.5, NONE, precision=precision, batch=n_s) as r:
+            r.set_state(u + lift)
+            spectra.append(r.structure_factor())
+    assert spectra[0].max() > 0
+    np.testing.assert_array_equal(spectra[1], spectra[0])
+    np.testing.assert_array_equal(spectra[2], spectra[0])
 
 
 @pytest.mark.parametrize("precision,tol", [(FP64, 1e-12), (FP32, 1e-6)])

@@ -20,7 +20,7 @@ import ctypes
 import numpy as np
 import pytest
 
-from qew_workloads import SEED
+from qew_workloads import SEED, random_state
 
 pytestmark = pytest.mark.gpu
 
@@ -29,14 +29,20 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-@pytest.mark.parametrize("kind,f,L,batch", [(0, 0.72057, 5000, 3), (1, 0.90749, 3001, 2), (2, 0.4, 700, 1),
-                                            (3, 1.5652, 2049, 2), (4, 1.9, 1500, 2), (0, 0.9, 300, 70)])
-def test_noalloc_matches_observe(orc, kind, f, L, batch):
+@pytest.mark.parametrize("kind,f,L,batch,base", [(0, 0.72057, 5000, 3, None), (1, 0.90749, 3001, 2, None),
+                                                 (2, 0.4, 700, 1, None), (3, 1.5652, 2049, 2, None),
+                                                 (4, 1.9, 1500, 2, None), (0, 0.9, 300, 70, None),
+                                                 (0, 1.0, 3000, 2, 2.0 ** 29 + 0.25), (1, 1.9, 2000, 2, -(2.0 ** 29) - 0.75)])
+def test_noalloc_matches_observe(orc, kind, f, L, batch, base):
+    """``base``: the chains start from a rough line around that height instead of the flat line
+    (cells near +-2^29: the sums are taken relative to each chain's first cell)."""
     torch = pytest.importorskip("torch")
     import paper_1211_7275_gb300 as q
     lib = q.load()
     steps = [0, 37, 300]
     with q.Relaxation(L, f, kind, dt=0.1, seed=SEED, batch=batch) as r:
+        if base is not None:
+            r.set_state(base + random_state(L * batch, 0.5, seed=41))
         obs = r.observe(steps)
         u, _ = r.state()
         cells = r.cells()
