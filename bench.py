@@ -420,7 +420,7 @@ def main() -> None:
     achieved = ops_per_su * su_per_launch / (per_launch_ms / 1e3) / 1e12
     peak = sms * LANES_PER_SM * clk * 1e6 / 1e12
     tile_w, K, tpc = tuning
-    bytes_per_su = sum(w * 2 * (8 + 4 * (4 if k in QUAD_KINDS else 2 if k != 2 else 0)) for k, w in wk.items()) / K
+    bytes_per_su = sum(w * 2 * (8 + 4 * (6 if k in QUAD_KINDS else 2 if k != 2 else 0)) for k, w in wk.items()) / K
     hbm_achieved = bytes_per_su * su_per_launch / (per_launch_ms / 1e3) / 1e9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     traffic = profiled_traffic()

@@ -187,7 +187,10 @@ void free_split(qew_ctx* h)
         dev_free(h->sp[b].cell);
         dev_free(h->sp[b].off);
         dev_free(h->sp[b].rf);
-        dev_free(h->sp[b].rb);
+        dev_free(h->sp[b].qn);
+        dev_free(h->sp[b].q3);
+        dev_free(h->sp[b].qab);
+        dev_free(h->sp[b].qc);
     }
 }
 
@@ -256,8 +259,12 @@ int alloc_state(qew_ctx* h)
             QEW_CUDA(h, dev_alloc(&h->sp[b].off, N), "allocating the offset array");
             if (h->kinds_mask & kPairMask)
                 QEW_CUDA(h, dev_alloc(&h->sp[b].rf, N), "allocating the two-node disorder cache");
-            if (h->kinds_mask & kQuadMask)
-                QEW_CUDA(h, dev_alloc(&h->sp[b].rb, N), "allocating the four-node disorder cache");
+            if (h->kinds_mask & kQuadMask) {
+                QEW_CUDA(h, dev_alloc(&h->sp[b].qn, N), "allocating the cubic disorder cache");
+                QEW_CUDA(h, dev_alloc(&h->sp[b].q3, N), "allocating the cubic disorder cache");
+                QEW_CUDA(h, dev_alloc(&h->sp[b].qab, N), "allocating the cubic disorder cache");
+                QEW_CUDA(h, dev_alloc(&h->sp[b].qc, N), "allocating the cubic disorder cache");
+            }
         }
     } else {
         free_split(h);

@@ -22,7 +22,8 @@ constexpr int kRBGCubic = 4;   // random bond: Gaussian G, Catmull-Rom spline (C
 constexpr int kNumKinds = 5;
 
 // Cache families: "pair" kinds keep the two nodes of the current cell per site, "quad" kinds
-// the four nodes V(n-1 .. n+2) of the cubic spline.
+// the cubic spline's coefficients over the cell (from the four nodes V(n-1 .. n+2)) and the
+// nodes V(n), V(n+1), V(n+2).
 __host__ __device__ constexpr bool pair_kind(int k) { return k == kRF || k == kRBGLinear; }
 __host__ __device__ constexpr bool quad_kind(int k) { return k == kRB || k == kRBGCubic; }
 constexpr int kPairMask = (1 << kRF) | (1 << kRBGLinear);

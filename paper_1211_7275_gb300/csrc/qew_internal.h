@@ -12,13 +12,18 @@
 namespace qew {
 
 // FP32-split state: cell n (int32), in-cell offset d (float, [0,1)) and the disorder cache
-// of each site, interleaved per site: RF keeps (R(n) + f, R(n+1) + f) in rf, RB keeps
-// (V(n-1), V(n), V(n+1), V(n+2)) in rb.  A chain of kind NONE uses neither.
+// of each site.  The two-node kinds keep (R(n) + f, R(n+1) + f) or (G(n), G(n+1)) in rf.  The
+// cubic kinds keep the nodes V(n), V(n+1) in qn, V(n+2) in q3, and the coefficients of
+// F_p + f = A + d (B + d C) over cell n (from V(n-1) .. V(n+2)) in qab (A, B) and qc (C).  A
+// chain of kind NONE uses none of them.
 struct SplitState {
     int32_t* cell;
     float* off;
     float2* rf;
-    float4* rb;
+    float2* qn;
+    float* q3;
+    float2* qab;
+    float* qc;
 };
 
 // FP64 state: displacement u, and the disorder cache of the cell `ncache` it was drawn for:

@@ -11,8 +11,9 @@
 // plus its disorder cache, held in shared memory.  Pair kinds keep the two nodes of the cell:
 // RF (R(n) + f, R(n+1) + f) -- the drive f is folded in, so F_p + f is one subtraction and one
 // FMA -- and the linear-spline random bond (G(n), G(n+1)), F_p + f = (G(n) - G(n+1)) + f.  Quad
-// kinds (cubic random bond, uniform V or Gaussian G) keep V(n-1 .. n+2) with the cubic
-// coefficients A, B, C of F_p + f = A + d (B + d C) beside them.
+// kinds (cubic random bond, uniform V or Gaussian G) keep the coefficients A, B, C of
+// F_p + f = A + d (B + d C) over the cell (from the spline nodes V(n-1 .. n+2)) and the three
+// nodes V(n), V(n+1), V(n+2) that a move to a neighbouring cell reuses.
 //
 // Work decomposition: one warp owns one tile of 32 * S sites of a chain, S consecutive sites
 // per lane.  A tile advanced K steps needs K extra sites on each side (the stencil's light
@@ -60,7 +61,7 @@ __device__ __forceinline__ int32_t site_index(int64_t wstart, int x, bool contig
 // Bytes of disorder cache per site in HBM.
 template <int KIND>
 struct CacheBytes {
-    static constexpr int hbm = pair_kind(KIND) ? 8 : quad_kind(KIND) ? 16 : 0;
+    static constexpr int hbm = pair_kind(KIND) ? 8 : quad_kind(KIND) ? 24 : 0;
 };
 
 // Shared memory per site.  Random-field tiles of 31 or more sites per lane use a compact layout
@@ -70,15 +71,19 @@ struct CacheBytes {
 // tiles are register-limited, and there the two-pass staging only costs (measured on 736-site
 // random-field tiles in a mixed batch and on Case 3).  The other layouts keep 8 bytes of staging
 // (cell and offset side by side, the cell half doubling as the cache cell) plus the cache: a
-// node pair (8 B), or the four nodes and the three coefficients of the cubic kinds (28 B).  The
-// coefficients sit in two arrays, (A, B) pairs and C alone, so the update loop reads 12 bytes
-// per site and step rather than a 16-byte vector with an unused lane: the cubic kinds are bound
-// by the shared-memory data path (measured: +5% on the uniform random bond, 12 instead of 11
-// warps per SM at 480-site tiles, against one load instruction more per site).
+// node pair (8 B), or for the cubic kinds the coefficients and three nodes (24 B, the same in
+// HBM, so a tile loads them without recomputing the coefficients).  The cubic kinds are bound by
+// the shared-memory data path and by latency; measured on the uniform random bond:
+//   - the coefficients as (A, B) pairs and C alone, so the update loop reads 12 bytes per site
+//     and step rather than a 16-byte vector with an unused lane: +5% (12 instead of 11 warps per
+//     SM at 480-site tiles, one load instruction more per site);
+//   - three nodes instead of four (V(n-1) is dropped; a down move draws it again, and at the
+//     thresholds down moves are a few in 10^4) and no coefficient recompute at tile load: +10%
+//     (14 warps per SM, 108 instead of 124 registers).
 __host__ __device__ constexpr bool compact_layout(int kind, int S) { return kind == kRF && S >= 31; }
 __host__ __device__ constexpr int site_smem_bytes(int kind, int S)
 {
-    return compact_layout(kind, S) ? 4 + 8 + 2 : pair_kind(kind) ? 8 + 8 : quad_kind(kind) ? 8 + 28 : 8;
+    return compact_layout(kind, S) ? 4 + 8 + 2 : pair_kind(kind) ? 8 + 8 : quad_kind(kind) ? 8 + 24 : 8;
 }
 
 // Per warp after its sites: one chunk of 32 queued moves.
@@ -156,9 +161,10 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     // compact layout: staging at 0, the node pair at 4 TW, cache cells (low 16 bits) at 12 TW
     float2* s_rf = reinterpret_cast<float2*>(wsm + (kCompact ? 4 : 8) * TW);
     uint16_t* s_cc16 = reinterpret_cast<uint16_t*>(wsm + 12 * TW);
-    float4* s_rb = reinterpret_cast<float4*>(wsm + 8 * TW);     // quad values V(n-1..n+2)
-    float2* s_ab = reinterpret_cast<float2*>(wsm + 24 * TW);    // quad coefficients (A, B)
-    float* s_c = reinterpret_cast<float*>(wsm + 32 * TW);       // and C
+    float2* s_qn = reinterpret_cast<float2*>(wsm + 8 * TW);     // cubic nodes V(n), V(n+1)
+    float* s_q3 = reinterpret_cast<float*>(wsm + 16 * TW);      // and V(n+2)
+    float2* s_ab = reinterpret_cast<float2*>(wsm + 20 * TW);    // cubic coefficients (A, B)
+    float* s_c = reinterpret_cast<float*>(wsm + 28 * TW);       // and C
 
     const TileDesc td = a.tiles[tile];
     const ChainDesc ch = a.chains[td.chain];
@@ -198,8 +204,12 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                 tma_load_1d(s_off, a.in.off + p0, TW * 4, bar);
                 if constexpr (pair_kind(KIND))
                     tma_load_1d(s_rf, a.in.rf + p0, TW * 8, bar);
-                if constexpr (quad_kind(KIND))
-                    tma_load_1d(s_rb, a.in.rb + p0, TW * 16, bar);
+                if constexpr (quad_kind(KIND)) {
+                    tma_load_1d(s_qn, a.in.qn + p0, TW * 8, bar);
+                    tma_load_1d(s_q3, a.in.q3 + p0, TW * 4, bar);
+                    tma_load_1d(s_ab, a.in.qab + p0, TW * 8, bar);
+                    tma_load_1d(s_c, a.in.qc + p0, TW * 4, bar);
+                }
             }
         }
         const bool landed = __all_sync(kFull, mbar_wait(bar, 0));   // warp-uniform outcome
@@ -220,8 +230,12 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                 s_off[x] = __ldg(g_off + p);
             if constexpr (pair_kind(KIND))
                 s_rf[x] = __ldg(a.in.rf + p);
-            if constexpr (quad_kind(KIND))
-                s_rb[x] = __ldg(a.in.rb + p);
+            if constexpr (quad_kind(KIND)) {
+                s_qn[x] = __ldg(a.in.qn + p);
+                s_q3[x] = __ldg(a.in.q3 + p);
+                s_ab[x] = __ldg(a.in.qab + p);
+                s_c[x] = __ldg(a.in.qc + p);
+            }
         }
         __syncwarp();
     }
@@ -267,13 +281,6 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
         if constexpr (!kCompact)
             c[j] = static_cast<float>(s_cell[x] - N0);
         d[j] = s_off[x];
-        if constexpr (quad_kind(KIND)) {
-            const float4 p = s_rb[x];
-            float A, B, C;
-            rb_coefficients(p.x, p.y, p.z, p.w, f, A, B, C);
-            s_ab[x] = make_float2(A, B);
-            s_c[x] = C;
-        }
     }
     __syncwarp();   // the staging area becomes the request queue below
 
@@ -391,22 +398,35 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                                 q = make_float2(v, pair_node_f32<KIND>(a.keys, s, i, wrap_node(nn + 1, M), f));
                             s_rf[x] = q;
                         } else {
-                            // one new node: n+2 after an up move, n-1 otherwise
+                            // The spline over the new cell nn needs V(nn-1 .. nn+2).  The cache
+                            // holds V(n), V(n+1), V(n+2) of the old cell n: an up move draws
+                            // V(nn+2); a down move draws V(nn-1) and V(nn) (V(n-1) is not kept:
+                            // at the thresholds down moves are a few in 10^4); a far move draws
+                            // all four.
                             const float v =
                                 quad_node_f32<KIND>(a.keys, s, i, wrap_node(code == kMoveUp ? nn + 2 : nn - 1, M));
-                            const float4 o = s_rb[x];
-                            float4 p;
-                            if (code == kMoveUp)
-                                p = make_float4(o.y, o.z, o.w, v);
-                            else if (code == kMoveDown)
-                                p = make_float4(v, o.x, o.y, o.z);
-                            else
-                                p = make_float4(v, quad_node_f32<KIND>(a.keys, s, i, wrap_node(nn, M)),
-                                                quad_node_f32<KIND>(a.keys, s, i, wrap_node(nn + 1, M)),
-                                                quad_node_f32<KIND>(a.keys, s, i, wrap_node(nn + 2, M)));
-                            s_rb[x] = p;
+                            const float2 o = s_qn[x];
+                            float p0, p1, p2, p3;
+                            if (code == kMoveUp) {
+                                p0 = o.x;
+                                p1 = o.y;
+                                p2 = s_q3[x];
+                                p3 = v;
+                            } else {
+                                p0 = v;
+                                p1 = quad_node_f32<KIND>(a.keys, s, i, wrap_node(nn, M));
+                                if (code == kMoveDown) {
+                                    p2 = o.x;
+                                    p3 = o.y;
+                                } else {
+                                    p2 = quad_node_f32<KIND>(a.keys, s, i, wrap_node(nn + 1, M));
+                                    p3 = quad_node_f32<KIND>(a.keys, s, i, wrap_node(nn + 2, M));
+                                }
+                            }
+                            s_qn[x] = make_float2(p1, p2);
+                            s_q3[x] = p3;
                             float A, B, C;
-                            rb_coefficients(p.x, p.y, p.z, p.w, f, A, B, C);
+                            rb_coefficients(p0, p1, p2, p3, f, A, B, C);
                             s_ab[x] = make_float2(A, B);
                             s_c[x] = C;
                         }
@@ -528,7 +548,12 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                 if constexpr (pair_kind(KIND))
                     tma_store_1d(a.out.rf + out0, s_rf + K, cnt * 8);
                 if constexpr (quad_kind(KIND))
-                    tma_store_1d(a.out.rb + out0, s_rb + K, cnt * 16);
+                {
+                    tma_store_1d(a.out.qn + out0, s_qn + K, cnt * 8);
+                    tma_store_1d(a.out.q3 + out0, s_q3 + K, cnt * 4);
+                    tma_store_1d(a.out.qab + out0, s_ab + K, cnt * 8);
+                    tma_store_1d(a.out.qc + out0, s_c + K, cnt * 4);
+                }
                 tma_store_commit();
                 tma_store_wait_all();
             }
@@ -541,8 +566,12 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                 a.out.off[p] = s_off[x];
                 if constexpr (pair_kind(KIND))
                     a.out.rf[p] = s_rf[x];
-                if constexpr (quad_kind(KIND))
-                    a.out.rb[p] = s_rb[x];
+                if constexpr (quad_kind(KIND)) {
+                    a.out.qn[p] = s_qn[x];
+                    a.out.q3[p] = s_q3[x];
+                    a.out.qab[p] = s_ab[x];
+                    a.out.qc[p] = s_c[x];
+                }
             }
         }
     }
@@ -613,12 +642,19 @@ __global__ void split_init_kernel(const ChainDesc* chains, const TileDesc* tiles
             st.rf[p] = make_float2(rf_plus_f32(seed, ch.s, i, m1, ch.f32), rf_plus_f32(seed, ch.s, i, m2, ch.f32));
         else if (ch.kind == kRBGLinear)
             st.rf[p] = make_float2(rbg_f32(seed, ch.s, i, m1), rbg_f32(seed, ch.s, i, m2));
-        else if (ch.kind == kRB)
-            st.rb[p] = make_float4(rb_f32(seed, ch.s, i, m0), rb_f32(seed, ch.s, i, m1), rb_f32(seed, ch.s, i, m2),
-                                   rb_f32(seed, ch.s, i, m3));
-        else if (ch.kind == kRBGCubic)
-            st.rb[p] = make_float4(rbg_f32(seed, ch.s, i, m0), rbg_f32(seed, ch.s, i, m1),
-                                   rbg_f32(seed, ch.s, i, m2), rbg_f32(seed, ch.s, i, m3));
+        else if (ch.kind == kRB || ch.kind == kRBGCubic) {
+            const bool uni = ch.kind == kRB;
+            const float p0 = uni ? rb_f32(seed, ch.s, i, m0) : rbg_f32(seed, ch.s, i, m0);
+            const float p1 = uni ? rb_f32(seed, ch.s, i, m1) : rbg_f32(seed, ch.s, i, m1);
+            const float p2 = uni ? rb_f32(seed, ch.s, i, m2) : rbg_f32(seed, ch.s, i, m2);
+            const float p3 = uni ? rb_f32(seed, ch.s, i, m3) : rbg_f32(seed, ch.s, i, m3);
+            float A, B, C;
+            rb_coefficients(p0, p1, p2, p3, ch.f32, A, B, C);
+            st.qn[p] = make_float2(p1, p2);
+            st.q3[p] = p3;
+            st.qab[p] = make_float2(A, B);
+            st.qc[p] = C;
+        }
     }
 }
 
