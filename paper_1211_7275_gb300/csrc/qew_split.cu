@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                     incl += y;
             }
             const int qn = __shfl_sync(kFull, incl, 31);
-            n_cross += (lane == 0) ? static_cast<unsigned>(qn) : 0u;
+            n_cross += static_cast<unsigned>(qn);   // the same in every lane
             if constexpr (KIND != kNone) {
                 // each lane's walk resumes in the next chunk where it stopped
                 int q = incl - cnt;
@@ -345,13 +345,12 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                     while (m != 0 && q < base + 32) {
                         const int b = mask_ffs(m) - 1;
                         m &= m - 1;
-                        s_q[q - base] = (lane << 8) | b;
+                        s_q[q - base] = lane * S + b;   // window position of the site
                         ++q;
                     }
                     __syncwarp();
                     if (base + lane < qn) {
-                        const int e = s_q[lane];
-                        const int x = (e >> 8) * S + (e & 0xff);
+                        const int x = s_q[lane];
                         const int nn = N0 + __float2int_rn(s_newc[x]);
                         int move;   // cells moved in this step
                         if constexpr (kCompact) {
@@ -365,7 +364,8 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                             s_ccell[x] = nn;
                         }
                         const int code = (move == 1) ? kMoveUp : (move == -1) ? kMoveDown : kMoveFar;
-                        const int32_t i = site_index(wstart, x, contiguous, L);
+                        const int32_t i = contiguous ? static_cast<int32_t>(wstart) + x
+                                                     : site_index(wstart, x, contiguous, L);
                         if constexpr (pair_kind(KIND) && S < 31) {
                             // one new node, n+1 after an up move and n after a down move; a far move
                             // draws n and n+1.  One call site, with a second trip only for far moves:
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     }
 
     if (a.crossings) {
-        const unsigned tot = __reduce_add_sync(kFull, n_cross);
+        const unsigned tot = n_cross;
         if (lane == 0 && tot)
             atomicAdd(a.crossings, static_cast<unsigned long long>(tot));
     }
