@@ -16,7 +16,7 @@ from qew_workloads import SEED, cosine_profile, log_spaced_steps, positive_shift
 
 pytestmark = pytest.mark.gpu
 
-RF, RB, NONE = 0, 1, 2
+RF, RB, NONE, RBG_LINEAR, RBG_CUBIC = 0, 1, 2, 3, 4
 FP32, FP64 = 0, 1
 
 
@@ -574,24 +574,38 @@ def test_full_size_uneven_256(qew, orc):
     _sampled_sites_check(qew, orc, L, f, kinds, 256, 600, 2, chains_to_check=chains)
 
 
-def test_steep_state_within_the_exact_range(qew, orc):
+@pytest.mark.parametrize("kind", [RF, RB, RBG_LINEAR, RBG_CUBIC])
+def test_steep_state_within_the_exact_range(qew, orc, kind):
     """A valid but extreme state: a triangle wave rising by 4000 cells per site (below the 2^12
     limit on neighbouring displacements that qew_set_state enforces), so a tile window spans
     millions of cells.  The range guard at the end of each call checks the neighbour
     differences of such windows and must not raise; the cells relative to a tile's reference stay
     exact floats (below 2^24), and per site the FP32-split state follows the oracle over 100 steps
-    to FP32 precision relative to u (the Laplacian moves the peaks by hundreds of cells per step)."""
+    to FP32 precision relative to u.  The Laplacian moves the peaks and valleys by hundreds of
+    cells per step in both directions, so every disorder kind takes its multi-cell (all nodes
+    drawn) and downward cache updates here, in every step."""
     L, f, n = 3000, 0.5, 100
     i = np.arange(L)
     tri = np.minimum(i % 600, 600 - i % 600)
     u0 = 4000.0 * tri + 0.25
     steps = np.array([0, 1, 10, n])
-    obs, u, _ = gpu_run(qew, L, f, RF, steps, FP32, u0=u0)
-    ref = orc.run(L, f, 0.1, RF, SEED, steps, u0=u0, want_state=True)
+    obs, u, _ = gpu_run(qew, L, f, kind, steps, FP32, u0=u0)
+    ref = orc.run(L, f, 0.1, kind, SEED, steps, u0=u0, want_state=True)
     # FP32 keeps the Laplacian's neighbour differences of ~4000 cells to 2^-24 relative, so the
     # per-site error scales with the local slope, not with 1e-4 cells
     rel = np.abs(u - ref["u"]) / np.maximum(1.0, np.abs(ref["u"]))
-    assert rel.max() <= 1e-7, rel.max()
+    bar = 1e-7
+    if kind == RBG_LINEAR:
+        # Case 3's force is piecewise constant: where the FP32 and the FP64 floor of a site
+        # disagree, its force jumps by |G(n) - G(n+1)| = O(1).  Here the rounding scale of a step is
+        # 4000 * 2^-24 = 2.4e-4 cells, and the exact dynamics itself moves by about 1e-5 relative
+        # under a start perturbation of that size (1e-8 for the continuous forces), so that is the
+        # bar.
+        rng = np.random.default_rng(61)
+        pert = orc.run(L, f, 0.1, kind, SEED, [n], u0=u0 + rng.uniform(-2.4e-4, 2.4e-4, L), want_state=True)["u"]
+        bar = float(np.max(np.abs(pert - ref["u"]) / np.maximum(1.0, np.abs(ref["u"]))))
+        print(f"Case 3: FP32-split vs oracle {rel.max():.2e}; the oracle under a 2.4e-4 start perturbation {bar:.2e}")
+    assert rel.max() <= bar, (rel.max(), bar)
     # the fused sums are FP32 relative to a cell of each tile: error at most gamma_40 * D with D the
     # spread of a tile window (here 992 * 4000 cells; see tests/test_gpu_observables.py)
     D = 992 * 4000.0 + 1.0
