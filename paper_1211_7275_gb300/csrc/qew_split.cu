@@ -27,11 +27,12 @@
 // bit per moved site.  After the update loop each lane stores its cells to shared memory (one
 // store per site; a store inside the update loop would keep the compiler from hoisting the cache
 // loads there), and a warp prefix sum of the lanes' move counts gives each lane its queue slots,
-// which it fills by walking the set bits of its mask, 32 slots per chunk, resuming in the next
-// chunk where it stopped (no atomics, deterministic order).  The queued Philox values are then
-// evaluated 32 lanes at a time and
-// written straight into the shared-memory cache of the requesting sites; the direction of each
-// move is recovered from the cell the cache was drawn for, kept per site in shared memory.
+// which it fills by walking the set bits of its mask (no atomics, deterministic order): all of
+// a step's requests in one pass where the queue holds a whole step, else 32 slots per chunk,
+// resuming in the next chunk where it stopped.  The queued Philox values are then evaluated 32
+// lanes at a time and written straight into the shared-memory cache of the requesting sites; the
+// direction of each move is recovered from the cell the cache was drawn for, kept per site in
+// shared memory.
 #include <cstdio>
 #include <mutex>
 #include <type_traits>
@@ -86,8 +87,15 @@ __host__ __device__ constexpr int site_smem_bytes(int kind, int S)
     return compact_layout(kind, S) ? 4 + 8 + 2 : pair_kind(kind) ? 8 + 8 : quad_kind(kind) ? 8 + 24 : 8;
 }
 
-// Per warp after its sites: one chunk of 32 queued moves.
-constexpr int kQueueBytes = 32 * 4;
+// Per warp after its sites, the request queue.  The two-node kinds below 31 sites per lane have
+// shared memory to spare: their queue holds every request of a step (a 16-bit window position per
+// site of the tile), so each lane walks its move mask once per step instead of once per chunk of
+// 32 requests (measured: Case 3, about 90 requests per step and tile, +18.5%; the random field at
+// 736-site tiles +2.5%).  The others keep one chunk of 32 requests: the compact random-field
+// layout and the cubic kinds are bound by shared memory, and their steps rarely make more than 32
+// requests.
+__host__ __device__ constexpr bool full_queue(int kind, int S) { return pair_kind(kind) && S < 31; }
+__host__ __device__ constexpr int queue_bytes(int kind, int S) { return full_queue(kind, S) ? 32 * S * 2 : 32 * 4; }
 
 // F_p + f at window position x with offset d, from the shared-memory cache.
 template <int KIND>
@@ -140,7 +148,8 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
 {
     constexpr int TW = 32 * S;
     constexpr bool kCompact = compact_layout(KIND, S);
-    constexpr int WARP_SMEM = TW * site_smem_bytes(KIND, S) + kQueueBytes;
+    constexpr bool kFullQueue = full_queue(KIND, S);
+    constexpr int WARP_SMEM = TW * site_smem_bytes(KIND, S) + queue_bytes(KIND, S);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t s_bar[8];
 
@@ -158,6 +167,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
     int32_t* s_ccell = s_cell;
     float* s_newc = s_off;
     int* s_q = reinterpret_cast<int*>(wsm + TW * site_smem_bytes(KIND, S));   // request chunk
+    uint16_t* s_q16 = reinterpret_cast<uint16_t*>(s_q);                       // or all of a step
     // compact layout: staging at 0, the node pair at 4 TW, cache cells (low 16 bits) at 12 TW
     float2* s_rf = reinterpret_cast<float2*>(wsm + (kCompact ? 4 : 8) * TW);
     uint16_t* s_cc16 = reinterpret_cast<uint16_t*>(wsm + 12 * TW);
@@ -341,16 +351,28 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
                 // each lane's walk resumes in the next chunk where it stopped
                 int q = incl - cnt;
                 MoveMask<S> m = mv;
-                for (int base = 0; base < qn; base += 32) {
-                    while (m != 0 && q < base + 32) {
+                if constexpr (kFullQueue) {
+                    // every request of the step at once (a site is queued at most once: qn <= TW)
+                    while (m != 0) {
                         const int b = mask_ffs(m) - 1;
                         m &= m - 1;
-                        s_q[q - base] = lane * S + b;   // window position of the site
+                        s_q16[q] = static_cast<uint16_t>(lane * S + b);
                         ++q;
                     }
                     __syncwarp();
+                }
+                for (int base = 0; base < qn; base += 32) {
+                    if constexpr (!kFullQueue) {
+                        while (m != 0 && q < base + 32) {
+                            const int b = mask_ffs(m) - 1;
+                            m &= m - 1;
+                            s_q[q - base] = lane * S + b;   // window position of the site
+                            ++q;
+                        }
+                        __syncwarp();
+                    }
                     if (base + lane < qn) {
-                        const int x = s_q[lane];
+                        const int x = kFullQueue ? static_cast<int>(s_q16[base + lane]) : s_q[lane];
                         const int nn = N0 + __float2int_rn(s_newc[x]);
                         int move;   // cells moved in this step
                         if constexpr (kCompact) {
@@ -580,7 +602,7 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND, S>::value) split_step_ker
 template <int KIND, int S>
 cudaError_t launch_split(int tiles_per_cta, const SplitLaunch& a, cudaStream_t st)
 {
-    const size_t smem = static_cast<size_t>(tiles_per_cta) * (32 * S * site_smem_bytes(KIND, S) + kQueueBytes);
+    const size_t smem = static_cast<size_t>(tiles_per_cta) * (32 * S * site_smem_bytes(KIND, S) + queue_bytes(KIND, S));
     auto kern = split_step_kernel<KIND, S>;
     // raise the dynamic shared-memory limit of this kernel on this device to the largest shape in
     // use; under a lock, so that two threads raising it at once cannot leave the smaller value
@@ -688,7 +710,7 @@ bool split_supported(int kind, int S)
 
 size_t split_smem_bytes(int kind, int S, int tiles_per_cta)
 {
-    return static_cast<size_t>(tiles_per_cta) * (32 * S * site_smem_bytes(kind, S) + kQueueBytes);
+    return static_cast<size_t>(tiles_per_cta) * (32 * S * site_smem_bytes(kind, S) + queue_bytes(kind, S));
 }
 
 cudaError_t split_step(int kind, int S, int tiles_per_cta, const SplitLaunch& a, cudaStream_t st)
